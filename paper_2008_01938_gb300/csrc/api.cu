@@ -1,0 +1,629 @@
+// api.cu -- host side of the C ABI declared in include/dpgpu.h: argument
+// validation, the diagonal-ordered MCM work queue, workspaces and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <list>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "api_internal.h"
+
+namespace dph {
+
+namespace {
+thread_local std::string t_err = "no error";
+std::mutex g_mu;
+std::map<int, DevState> g_dev;
+
+constexpr int T = dpk::kTile;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+}  // namespace
+
+dp_status fail(dp_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+dp_status fail_cuda(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? DP_ENOMEM : DP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+long long spin_limit() {
+  const char* s = getenv("DPGPU_SPIN_LIMIT");
+  if (s && *s) {
+    const long long v = atoll(s);
+    if (v > 0) return v;
+  }
+  return 1ll << 32;  // about two seconds of SM clock
+}
+
+dp_status current_dev(DevState** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_dev.find(dev);
+  if (it != g_dev.end()) {
+    *out = &it->second;
+    return DP_OK;
+  }
+  DevState ds;
+  ds.device = dev;
+  if ((e = cudaDeviceGetAttribute(&ds.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return fail_cuda(e, "cudaDeviceGetAttribute");
+  for (int c = 0; c < 2; ++c) {
+    if ((e = dpk::mcm_configure(c == 1)) != cudaSuccess) return fail_cuda(e, "configure MCM kernel");
+    if ((e = dpk::mcm_occupancy(c == 1, &ds.occ[c])) != cudaSuccess) return fail_cuda(e, "MCM occupancy");
+    if (ds.occ[c] < 1) ds.occ[c] = 1;
+  }
+  if ((e = cudaMalloc(&ds.status, 256)) != cudaSuccess) return fail_cuda(e, "cudaMalloc(status)");
+  if ((e = cudaMemset(ds.status, 0, 256)) != cudaSuccess) return fail_cuda(e, "cudaMemset(status)");
+  // keep freed stream-ordered allocations cached in the pool
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  auto res = g_dev.emplace(dev, ds);
+  *out = &res.first->second;
+  return DP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// MCM: static plan (task queue) construction
+// ---------------------------------------------------------------------------
+
+McmStatic::~McmStatic() {
+  if (device >= 0 && owns_device) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != device) cudaSetDevice(device);
+    cudaFree(d_tasks);
+    cudaFree(d_accslot);
+    cudaFree(d_insts);
+    if (cur >= 0 && cur != device) cudaSetDevice(cur);
+  }
+}
+
+namespace {
+// Levels of ready-diagonal grouped into one bulk task, and the smallest number
+// of bulk levels for which a tile is split at all.
+constexpr int kLevelsPerPart = 4;
+constexpr int kMinBulkLevels = 2;
+
+struct SortKey {
+  int32_t bucket, kind, inst, I, J;
+  bool operator<(const SortKey& o) const {
+    return std::tie(bucket, kind, inst, I, J) < std::tie(o.bucket, o.kind, o.inst, o.I, o.J);
+  }
+};
+}  // namespace
+
+dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared_ptr<McmStatic>* out, bool upload) {
+  auto sp = std::make_shared<McmStatic>();
+  sp->i64 = i64;
+  sp->ns = ns;
+  int64_t tile_base = 0, pp_base = 0, pk_base = 0;
+  for (size_t b = 0; b < ns.size(); ++b) {
+    const int32_t n = ns[b];
+    if (n < 1 || n > 32767) return fail(DP_EINVAL, "chain %zu: n = %d outside [1, 32767]", b, n);
+    dpk::McmInstDev in{};
+    in.n = n;
+    in.nt = (n + T - 1) / T;
+    in.tile_base = tile_base;
+    in.pp_base = pp_base;
+    in.pk_base = pk_base;
+    sp->insts.push_back(in);
+    tile_base += (int64_t)in.nt * (in.nt + 1) / 2;
+    pp_base += (int64_t)in.nt * T + 32;
+    pk_base += (int64_t)in.nt * T;
+    sp->split_evals += ((double)n * n * n - n) / 6.0;
+  }
+  sp->ntiles = tile_base;
+  sp->pp_total = pp_base;
+  sp->pk_total = pk_base;
+  sp->accslot.assign((size_t)tile_base, -1);
+
+  std::vector<std::pair<SortKey, dpk::McmTask>> items;
+  for (size_t b = 0; b < ns.size(); ++b) {
+    const dpk::McmInstDev& in = sp->insts[b];
+    const int nt = in.nt;
+    for (int I = 0; I < nt; ++I) {
+      for (int J = I; J < nt; ++J) {
+        const int D = J - I;
+        const int64_t tix = in.tile_base + (int64_t)I * nt - (int64_t)I * (I - 1) / 2 + (J - I);
+        dpk::McmTask fin{};
+        fin.inst = (int32_t)b;
+        fin.I = (int16_t)I;
+        fin.J = (int16_t)J;
+        fin.kind = 0;
+        fin.r_lo = 1;
+        fin.r_hi = 0;  // empty range
+        if (D >= 2) {
+          const int rmin = (D + 1) / 2, rmax = D - 1;
+          int fin_lo = rmax;  // the finisher keeps the last level (both neighbours)
+          if (fin_lo - rmin < kMinBulkLevels) fin_lo = rmin;
+          int nparts = 0;
+          for (int r0 = rmin; r0 < fin_lo; r0 += kLevelsPerPart) {
+            const int r1 = std::min(r0 + kLevelsPerPart - 1, fin_lo - 1);
+            dpk::McmTask part{};
+            part.inst = (int32_t)b;
+            part.I = (int16_t)I;
+            part.J = (int16_t)J;
+            part.r_lo = (int16_t)r0;
+            part.r_hi = (int16_t)r1;
+            part.kind = 1;
+            items.push_back({SortKey{r1 + 1, 1, (int32_t)b, I, J}, part});
+            ++nparts;
+          }
+          if (nparts > 0) sp->accslot[(size_t)tix] = (int32_t)sp->nslots++;
+          fin.r_lo = (int16_t)fin_lo;
+          fin.r_hi = (int16_t)rmax;
+          fin.nparts = (int16_t)nparts;
+        }
+        items.push_back({SortKey{D, 0, (int32_t)b, I, J}, fin});
+      }
+    }
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<SortKey, dpk::McmTask>& x, const std::pair<SortKey, dpk::McmTask>& y) {
+                     return x.first < y.first;
+                   });
+  sp->tasks.reserve(items.size());
+  for (auto& it : items) sp->tasks.push_back(it.second);
+
+  if (!upload) {
+    *out = sp;
+    return DP_OK;
+  }
+  cudaError_t e;
+  if ((e = cudaGetDevice(&sp->device)) != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  const size_t tb = sp->tasks.size() * sizeof(dpk::McmTask);
+  const size_t ab = sp->accslot.size() * sizeof(int32_t);
+  const size_t ib = sp->insts.size() * sizeof(dpk::McmInstDev);
+  if ((e = cudaMalloc(&sp->d_tasks, std::max<size_t>(tb, 16))) != cudaSuccess) return fail_cuda(e, "cudaMalloc(tasks)");
+  if ((e = cudaMalloc(&sp->d_accslot, std::max<size_t>(ab, 16))) != cudaSuccess) return fail_cuda(e, "cudaMalloc(accslot)");
+  if ((e = cudaMalloc(&sp->d_insts, std::max<size_t>(ib, 16))) != cudaSuccess) return fail_cuda(e, "cudaMalloc(insts)");
+  if (tb && (e = cudaMemcpy(sp->d_tasks, sp->tasks.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail_cuda(e, "upload tasks");
+  if (ab && (e = cudaMemcpy(sp->d_accslot, sp->accslot.data(), ab, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail_cuda(e, "upload accslot");
+  if (ib && (e = cudaMemcpy(sp->d_insts, sp->insts.data(), ib, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail_cuda(e, "upload instances");
+  *out = sp;
+  return DP_OK;
+}
+
+McmLayout mcm_layout(const McmStatic& sp) {
+  McmLayout L;
+  const size_t es = sp.i64 ? 8 : 4;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 16), 256);
+    return o;
+  };
+  L.af = take((size_t)sp.ntiles * T * T * es);
+  L.bf = take((size_t)sp.ntiles * T * T * es);
+  L.zero_begin = off;
+  L.flags = take((size_t)sp.ntiles * 4);
+  L.counters = take((size_t)sp.ntiles * 4);
+  L.queue = take(16);
+  L.zero_bytes = off - L.zero_begin;
+  L.acc = take((size_t)sp.nslots * T * T * 8);
+  L.pp = take((size_t)sp.pp_total * 4);
+  L.pk = take((size_t)sp.pk_total * 4);
+  L.insts = take(sp.insts.size() * sizeof(dpk::McmInstDev));
+  L.total = off;
+  return L;
+}
+
+dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const int32_t* p_all,
+                      const int64_t* p_off, const int64_t* tab_off, void* m_all, int16_t* s_all,
+                      int32_t* status, cudaStream_t st, long long limit_override, int32_t drop_task) {
+  DevState* ds = nullptr;
+  dp_status rc = current_dev(&ds);
+  if (rc != DP_OK) return rc;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(w + L.zero_begin, 0, L.zero_bytes, st)) != cudaSuccess) return fail_cuda(e, "memset flags");
+  if (sp.nslots > 0 && (e = cudaMemsetAsync(w + L.acc, 0xFF, (size_t)sp.nslots * T * T * 8, st)) != cudaSuccess)
+    return fail_cuda(e, "memset accumulators");
+  if ((e = cudaMemcpyAsync(w + L.insts, sp.d_insts, sp.insts.size() * sizeof(dpk::McmInstDev),
+                           cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return fail_cuda(e, "copy instances");
+  dpk::McmLaunchArgs a{};
+  a.insts = reinterpret_cast<dpk::McmInstDev*>(w + L.insts);
+  a.tasks = sp.d_tasks;
+  a.ninst = (int32_t)sp.insts.size();
+  a.ntasks = (int32_t)sp.tasks.size();
+  a.af = w + L.af;
+  a.bf = w + L.bf;
+  a.flags = reinterpret_cast<int32_t*>(w + L.flags);
+  a.counters = reinterpret_cast<int32_t*>(w + L.counters);
+  a.accslot = sp.d_accslot;
+  a.acc = reinterpret_cast<unsigned long long*>(w + L.acc);
+  a.pp = reinterpret_cast<int32_t*>(w + L.pp);
+  a.pk = reinterpret_cast<uint32_t*>(w + L.pk);
+  a.queue = reinterpret_cast<int32_t*>(w + L.queue);
+  a.status = status ? status : ds->status;
+  a.spin_limit = limit_override > 0 ? limit_override : spin_limit();
+  a.drop_task = drop_task;
+  a.p_all = p_all;
+  a.p_off = p_off;
+  a.tab_off = tab_off;
+  a.m_all = m_all;
+  a.s_all = s_all;
+  if ((e = dpk::launch_mcm_prologue(a, sp.i64, st)) != cudaSuccess) return fail_cuda(e, "launch MCM prologue");
+  const int c = sp.i64 ? 1 : 0;
+  const int grid = (int)std::min<int64_t>((int64_t)ds->sms * ds->occ[c], (int64_t)sp.tasks.size());
+  if ((e = dpk::launch_mcm_main(a, sp.i64, std::max(grid, 1), st)) != cudaSuccess)
+    return fail_cuda(e, "launch MCM kernel");
+  return DP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// S-DP helpers
+// ---------------------------------------------------------------------------
+dp_status sdp_validate(int64_t n, const int32_t* a, int32_t k, int op) {
+  if (op != DP_OP_MIN && op != DP_OP_ADD_MOD32) return fail(DP_EINVAL, "op must be DP_OP_MIN or DP_OP_ADD_MOD32");
+  if (k < 1 || k > dpk::kSdpMaxK) return fail(DP_EINVAL, "k = %d outside [1, %d]", k, dpk::kSdpMaxK);
+  if (!a) return fail(DP_EINVAL, "offsets pointer is NULL");
+  if (n < 0) return fail(DP_EINVAL, "n = %lld < 0", (long long)n);
+  for (int j = 0; j < k; ++j) {
+    if (a[j] < 1) return fail(DP_EINVAL, "offset a[%d] = %d < 1", j, a[j]);
+    if (j > 0 && a[j] >= a[j - 1])
+      return fail(DP_EINVAL, "offsets must be strictly decreasing (a[%d] = %d >= a[%d] = %d)", j, a[j], j - 1,
+                  a[j - 1]);
+  }
+  return DP_OK;
+}
+
+void sdp_shape(int32_t a1, int32_t ak, int* threads, int* ring_log2) {
+  int th = ak >= 1024 ? 1024 : ((ak + 31) / 32) * 32;
+  if (th < 32) th = 32;
+  const int W = std::min(ak, th);
+  int lg = 0;
+  while ((1ll << lg) < (long long)a1 + W) ++lg;
+  *threads = th;
+  *ring_log2 = lg <= dpk::kSdpRingMaxLog2 ? std::max(lg, 1) : 0;
+}
+
+}  // namespace dph
+
+using namespace dph;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+namespace {
+std::mutex g_cache_mu;
+// per (device, n, cost) static plans for single-chain solves
+std::list<std::tuple<int, int32_t, bool, std::shared_ptr<McmStatic>>> g_single_cache;
+
+dp_status single_plan(int32_t n, bool i64, std::shared_ptr<McmStatic>* out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  for (auto it = g_single_cache.begin(); it != g_single_cache.end(); ++it) {
+    if (std::get<0>(*it) == dev && std::get<1>(*it) == n && std::get<2>(*it) == i64) {
+      *out = std::get<3>(*it);
+      g_single_cache.splice(g_single_cache.begin(), g_single_cache, it);
+      return DP_OK;
+    }
+  }
+  std::shared_ptr<McmStatic> sp;
+  dp_status rc = mcm_build_static(std::vector<int32_t>{n}, i64, &sp);
+  if (rc != DP_OK) return rc;
+  g_single_cache.emplace_front(dev, n, i64, sp);
+  if (g_single_cache.size() > 32) g_single_cache.pop_back();
+  *out = sp;
+  return DP_OK;
+}
+
+struct McmPlan {
+  std::shared_ptr<McmStatic> sp;
+  McmLayout L;
+  void* ws = nullptr;
+  int device = -1;
+};
+
+struct SdpPlan {
+  int device = -1;
+  int32_t batch = 0;
+  int op = 0;
+  int threads = 32, ring_log2 = 0, kmax = 1;
+  dpk::SdpInstDev* d_insts = nullptr;
+  int32_t* d_offs = nullptr;
+};
+
+dp_status mcm_solve_impl(const int32_t* p, int32_t n, dp_cost ct, void* m, int16_t* s, int32_t* status_dev,
+                         cudaStream_t st, long long limit_override, int32_t drop_task) {
+  if (!p || !m || !s) return fail(DP_EINVAL, "mcm_solve: NULL pointer argument");
+  if (n < 1 || n > 32767) return fail(DP_EINVAL, "mcm_solve: n = %d outside [1, 32767]", n);
+  if (ct != DP_COST_I32 && ct != DP_COST_I64) return fail(DP_EINVAL, "mcm_solve: unknown cost type %d", (int)ct);
+  const bool i64 = ct == DP_COST_I64;
+  std::shared_ptr<McmStatic> sp;
+  dp_status rc = single_plan(n, i64, &sp);
+  if (rc != DP_OK) return rc;
+  const McmLayout L = mcm_layout(*sp);
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(&ws, L.total, st);
+  if (e != cudaSuccess) return fail_cuda(e, "mcm_solve: workspace allocation");
+  rc = mcm_enqueue(*sp, L, ws, p, nullptr, nullptr, m, s, status_dev, st, limit_override, drop_task);
+  e = cudaFreeAsync(ws, st);
+  if (rc != DP_OK) return rc;
+  if (e != cudaSuccess) return fail_cuda(e, "mcm_solve: workspace release");
+  return DP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+const char* dp_last_error(void) { return t_err.c_str(); }
+
+const char* dp_version(void) { return "dpgpu 0.1 (sm_103a)"; }
+
+dp_status dp_sync_status(void* stream, int32_t* status_dev) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail_cuda(e, "dp_sync_status: stream");
+  int32_t* word = status_dev;
+  if (!word) {
+    DevState* ds = nullptr;
+    dp_status rc = current_dev(&ds);
+    if (rc != DP_OK) return rc;
+    word = ds->status;
+  }
+  int32_t h = 0;
+  if ((e = cudaMemcpy(&h, word, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return fail_cuda(e, "read status");
+  if (h != 0) {
+    if ((e = cudaMemset(word, 0, 4)) != cudaSuccess) return fail_cuda(e, "clear status");
+    const char* what = h == DP_EINVAL      ? "invalid input found on the device (a dimension < 1?)"
+                       : h == DP_EOVERFLOW ? "cost bound does not fit the cost type"
+                       : h == DP_ETIMEOUT  ? "a bounded device-side wait timed out"
+                                           : "device error";
+    return fail((dp_status)h, "device status %d: %s", h, what);
+  }
+  return DP_OK;
+}
+
+dp_status mcm_solve(const int32_t* p, int32_t n, dp_cost ct, void* m, int16_t* s, int32_t* status_dev,
+                    void* stream) {
+  return mcm_solve_impl(p, n, ct, m, s, status_dev, static_cast<cudaStream_t>(stream), 0, -1);
+}
+
+// Fault-injection hook for tests: like mcm_solve, but queue entry `drop_task`
+// is popped and skipped, so the tiles waiting for it hit their bounded waits
+// (`spin_limit` clock cycles) and the status word reports DP_ETIMEOUT.
+dp_status dp_test_mcm_drop_task(const int32_t* p, int32_t n, dp_cost ct, void* m, int16_t* s,
+                                int32_t* status_dev, void* stream, int32_t drop_task, long long limit) {
+  return mcm_solve_impl(p, n, ct, m, s, status_dev, static_cast<cudaStream_t>(stream), limit, drop_task);
+}
+
+dp_status mcm_solve_host(const int32_t* p_host, int32_t n, dp_cost ct, void* m_host, int16_t* s_host,
+                         void* stream) {
+  if (!p_host || !m_host || !s_host) return fail(DP_EINVAL, "mcm_solve_host: NULL pointer argument");
+  if (n < 1 || n > 32767) return fail(DP_EINVAL, "mcm_solve_host: n = %d outside [1, 32767]", n);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t es = ct == DP_COST_I64 ? 8 : 4;
+  const size_t nn = (size_t)n * n;
+  uint8_t* buf = nullptr;
+  const size_t pb = align_up((size_t)(n + 1) * 4, 256), mb = align_up(nn * es, 256), sb = align_up(nn * 2, 256);
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), pb + mb + sb + 256, st);
+  if (e != cudaSuccess) return fail_cuda(e, "mcm_solve_host: allocation");
+  int32_t* d_status = reinterpret_cast<int32_t*>(buf + pb + mb + sb);
+  dp_status rc = DP_OK;
+  if ((e = cudaMemsetAsync(d_status, 0, 4, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(buf, p_host, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+    rc = fail_cuda(e, "mcm_solve_host: upload");
+  }
+  if (rc == DP_OK)
+    rc = mcm_solve_impl(reinterpret_cast<int32_t*>(buf), n, ct, buf + pb, reinterpret_cast<int16_t*>(buf + pb + mb),
+                        d_status, st, 0, -1);
+  if (rc == DP_OK) {
+    if ((e = cudaMemcpyAsync(m_host, buf + pb, nn * es, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(s_host, buf + pb + mb, nn * 2, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      rc = fail_cuda(e, "mcm_solve_host: download");
+  }
+  if (rc == DP_OK) rc = dp_sync_status(stream, d_status);
+  cudaFreeAsync(buf, st);
+  if (rc == DP_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = fail_cuda(e, "mcm_solve_host: sync");
+  return rc;
+}
+
+dp_status mcm_plan_create(int32_t batch, const int32_t* n_host, dp_cost ct, void** plan) {
+  if (!plan || (batch > 0 && !n_host) || batch < 0) return fail(DP_EINVAL, "mcm_plan_create: bad arguments");
+  if (ct != DP_COST_I32 && ct != DP_COST_I64) return fail(DP_EINVAL, "mcm_plan_create: unknown cost type");
+  DevState* ds = nullptr;
+  dp_status rc = current_dev(&ds);
+  if (rc != DP_OK) return rc;
+  auto* pl = new McmPlan();
+  rc = mcm_build_static(std::vector<int32_t>(n_host, n_host + batch), ct == DP_COST_I64, &pl->sp);
+  if (rc != DP_OK) {
+    delete pl;
+    return rc;
+  }
+  pl->L = mcm_layout(*pl->sp);
+  pl->device = ds->device;
+  cudaError_t e = cudaMalloc(&pl->ws, pl->L.total);
+  if (e != cudaSuccess) {
+    delete pl;
+    return fail_cuda(e, "mcm_plan_create: workspace");
+  }
+  *plan = pl;
+  return DP_OK;
+}
+
+dp_status mcm_solve_batched(void* plan, const int32_t* p_all, const int64_t* p_off, const int64_t* tab_off,
+                            void* m_all, int16_t* s_all, int32_t* status_dev, void* stream) {
+  auto* pl = static_cast<McmPlan*>(plan);
+  if (!pl || !p_all || !p_off || !tab_off || !m_all || !s_all)
+    return fail(DP_EINVAL, "mcm_solve_batched: NULL argument");
+  return mcm_enqueue(*pl->sp, pl->L, pl->ws, p_all, p_off, tab_off, m_all, s_all, status_dev,
+                     static_cast<cudaStream_t>(stream));
+}
+
+dp_status mcm_plan_destroy(void* plan) {
+  auto* pl = static_cast<McmPlan*>(plan);
+  if (!pl) return DP_OK;
+  cudaFree(pl->ws);
+  delete pl;
+  return DP_OK;
+}
+
+// Number of queue entries of a batched plan (for tests and benchmarks).
+int64_t dp_mcm_plan_tasks(void* plan) {
+  auto* pl = static_cast<McmPlan*>(plan);
+  return pl ? (int64_t)pl->sp->tasks.size() : -1;
+}
+
+dp_status sdp_solve(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, dp_op op, int32_t* status_dev,
+                    void* stream) {
+  if (!ST) return fail(DP_EINVAL, "sdp_solve: ST is NULL");
+  dp_status rc = sdp_validate(n, a, k, op);
+  if (rc != DP_OK) return rc;
+  if (n <= a[0]) return DP_OK;
+  DevState* ds = nullptr;
+  if ((rc = current_dev(&ds)) != DP_OK) return rc;
+  dpk::SdpLaunchArgs args{};
+  args.insts = nullptr;
+  args.one.st = ST;
+  args.one.n = n;
+  args.one.a = nullptr;
+  args.one.k = k;
+  args.ninst = 1;
+  args.op = (int32_t)op;
+  sdp_shape(a[0], a[k - 1], &args.threads, &args.ring_log2);
+  args.status = status_dev ? status_dev : ds->status;
+  for (int j = 0; j < k; ++j) args.one_offs[j] = a[j];
+  cudaError_t e = dpk::launch_sdp(args, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "sdp_solve: launch");
+  return DP_OK;
+}
+
+dp_status sdp_solve_host(uint32_t* ST_host, int64_t n, const int32_t* a, int32_t k, dp_op op, void* stream) {
+  if (!ST_host) return fail(DP_EINVAL, "sdp_solve_host: ST is NULL");
+  dp_status rc = sdp_validate(n, a, k, op);
+  if (rc != DP_OK) return rc;
+  if (n <= a[0]) return DP_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), (size_t)n * 4, st);
+  if (e != cudaSuccess) return fail_cuda(e, "sdp_solve_host: allocation");
+  if ((e = cudaMemcpyAsync(d, ST_host, (size_t)a[0] * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    rc = fail_cuda(e, "sdp_solve_host: upload");
+  if (rc == DP_OK) rc = sdp_solve(d, n, a, k, op, nullptr, stream);
+  if (rc == DP_OK && (e = cudaMemcpyAsync(ST_host, d, (size_t)n * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    rc = fail_cuda(e, "sdp_solve_host: download");
+  if (rc == DP_OK) rc = dp_sync_status(stream, nullptr);
+  cudaFreeAsync(d, st);
+  if (rc == DP_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = fail_cuda(e, "sdp_solve_host: sync");
+  return rc;
+}
+
+dp_status sdp_plan_create(int32_t batch, const int64_t* n_host, const int32_t* k_host, const int32_t* a_host,
+                          dp_op op, void** plan) {
+  if (!plan || batch < 0 || (batch > 0 && (!n_host || !k_host || !a_host)))
+    return fail(DP_EINVAL, "sdp_plan_create: bad arguments");
+  DevState* ds = nullptr;
+  dp_status rc = current_dev(&ds);
+  if (rc != DP_OK) return rc;
+  std::vector<dpk::SdpInstDev> insts((size_t)batch);
+  int64_t aoff = 0;
+  int kmax = 1, threads = 32, ring_log2 = 1;
+  bool ring_ok = true;
+  for (int b = 0; b < batch; ++b) {
+    const int32_t* a = a_host + aoff;
+    if ((rc = sdp_validate(n_host[b], a, k_host[b], op)) != DP_OK) return fail(rc, "instance %d: %s", b, t_err.c_str());
+    insts[b].n = n_host[b];
+    insts[b].k = k_host[b];
+    insts[b].a_off = (int32_t)aoff;
+    kmax = std::max(kmax, (int)k_host[b]);
+    int th, lg;
+    sdp_shape(a[0], a[k_host[b] - 1], &th, &lg);
+    threads = std::max(threads, th);
+    aoff += k_host[b];
+  }
+  // one block shape for the launch: recompute the ring for the widest step
+  for (int b = 0; b < batch; ++b) {
+    const int32_t* a = a_host + insts[b].a_off;
+    const int W = std::min(a[insts[b].k - 1], threads);
+    int lg = 0;
+    while ((1ll << lg) < (long long)a[0] + W) ++lg;
+    if (lg > dpk::kSdpRingMaxLog2) ring_ok = false;
+    ring_log2 = std::max(ring_log2, lg);
+  }
+  auto* pl = new SdpPlan();
+  pl->device = ds->device;
+  pl->batch = batch;
+  pl->op = (int)op;
+  pl->threads = threads;
+  pl->ring_log2 = ring_ok ? ring_log2 : 0;
+  pl->kmax = kmax;
+  cudaError_t e;
+  if ((e = cudaMalloc(&pl->d_offs, std::max<int64_t>(aoff, 4) * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&pl->d_insts, std::max<size_t>(insts.size(), 1) * sizeof(dpk::SdpInstDev))) != cudaSuccess) {
+    cudaFree(pl->d_offs);
+    delete pl;
+    return fail_cuda(e, "sdp_plan_create: allocation");
+  }
+  for (auto& in : insts) in.a = pl->d_offs + in.a_off;
+  if ((aoff && (e = cudaMemcpy(pl->d_offs, a_host, aoff * 4, cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (batch && (e = cudaMemcpy(pl->d_insts, insts.data(), insts.size() * sizeof(dpk::SdpInstDev),
+                                cudaMemcpyHostToDevice)) != cudaSuccess)) {
+    cudaFree(pl->d_offs);
+    cudaFree(pl->d_insts);
+    delete pl;
+    return fail_cuda(e, "sdp_plan_create: upload");
+  }
+  *plan = pl;
+  return DP_OK;
+}
+
+dp_status sdp_solve_batched(void* plan, uint32_t* ST_all, const int64_t* st_off, int32_t* status_dev,
+                            void* stream) {
+  auto* pl = static_cast<SdpPlan*>(plan);
+  if (!pl || !ST_all || !st_off) return fail(DP_EINVAL, "sdp_solve_batched: NULL argument");
+  if (pl->batch == 0) return DP_OK;
+  DevState* ds = nullptr;
+  dp_status rc = current_dev(&ds);
+  if (rc != DP_OK) return rc;
+  dpk::SdpLaunchArgs args{};
+  args.insts = pl->d_insts;
+  args.one.k = pl->kmax;
+  args.ninst = pl->batch;
+  args.op = pl->op;
+  args.threads = pl->threads;
+  args.ring_log2 = pl->ring_log2;
+  args.st_all = ST_all;
+  args.st_off = st_off;
+  args.status = status_dev ? status_dev : ds->status;
+  cudaError_t e = dpk::launch_sdp(args, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail_cuda(e, "sdp_solve_batched: launch");
+  return DP_OK;
+}
+
+dp_status sdp_plan_destroy(void* plan) {
+  auto* pl = static_cast<SdpPlan*>(plan);
+  if (!pl) return DP_OK;
+  cudaFree(pl->d_offs);
+  cudaFree(pl->d_insts);
+  delete pl;
+  return DP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// api_internal.h -- host-side helpers shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <memory>
+#include <vector>
+
+#include "dpgpu.h"
+#include "mcm_kernels.cuh"
+#include "sdp_kernels.cuh"
+
+namespace dph {
+
+// Records a thread-local error message and returns `code`.
+dp_status fail(dp_status code, const char* fmt, ...);
+dp_status fail_cuda(cudaError_t e, const char* what);
+
+struct DevState {
+  int device = -1;
+  int sms = 0;
+  int occ[2] = {0, 0};        // MCM blocks per SM, int32 / int64 costs
+  int32_t* status = nullptr;  // library-owned status word
+};
+
+// Per-device state for the current device (created on first use).
+dp_status current_dev(DevState** out);
+
+long long spin_limit();     // bounded-wait budget in clock cycles
+
+// ---------------------------------------------------------------------------
+// MCM plans
+// ---------------------------------------------------------------------------
+struct McmStatic {
+  bool i64 = false;
+  int device = -1;
+  std::vector<int32_t> ns;
+  std::vector<dpk::McmInstDev> insts;   // static fields only
+  std::vector<dpk::McmTask> tasks;
+  std::vector<int32_t> accslot;
+  int64_t ntiles = 0, nslots = 0, pp_total = 0, pk_total = 0;
+  double split_evals = 0;
+  // device copies (immutable after creation)
+  dpk::McmTask* d_tasks = nullptr;
+  int32_t* d_accslot = nullptr;
+  dpk::McmInstDev* d_insts = nullptr;
+  bool owns_device = true;               // false: device pointers borrowed from a workspace
+  ~McmStatic();
+};
+
+struct McmLayout {
+  size_t af = 0, bf = 0, flags = 0, counters = 0, queue = 0, acc = 0, pp = 0, pk = 0, insts = 0;
+  size_t zero_begin = 0, zero_bytes = 0, total = 0;
+};
+
+// Builds the work queue on the host; with upload=true also copies the queue,
+// slot table and chain records to fresh device memory owned by the result.
+dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared_ptr<McmStatic>* out,
+                           bool upload = true);
+McmLayout mcm_layout(const McmStatic& sp);
+// Enqueues memsets + prologue + main kernel for a static plan on `ws`.
+dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const int32_t* p_all,
+                      const int64_t* p_off, const int64_t* tab_off, void* m_all, int16_t* s_all,
+                      int32_t* status, cudaStream_t st, long long limit_override = 0,
+                      int32_t drop_task = -1);
+
+// ---------------------------------------------------------------------------
+// S-DP
+// ---------------------------------------------------------------------------
+dp_status sdp_validate(int64_t n, const int32_t* a, int32_t k, int op);
+void sdp_shape(int32_t a1, int32_t ak, int* threads, int* ring_log2);
+
+}  // namespace dph

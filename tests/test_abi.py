@@ -1,0 +1,67 @@
+"""The native library builds, loads without a GPU, and exports every function
+declared in include/dpgpu.h (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "dpgpu.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2008_01938_gb300 import build, native
+    build.build()
+    return ctypes.CDLL(native.LIB_PATH)
+
+
+def test_header_lists_the_boundary():
+    names = header_functions()
+    for expected in ["mcm_solve", "mcm_solve_batched", "mcm_plan_create", "sdp_solve", "sdp_solve_batched",
+                     "serve_submit", "serve_poll", "dp_sync_status", "dp_last_error"]:
+        assert expected in names
+
+
+def test_library_exports_every_header_symbol(lib):
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, f"symbols declared in dpgpu.h but not exported: {missing}"
+
+
+def test_binding_symbol_list_matches_header():
+    from paper_2008_01938_gb300 import native
+    assert sorted(native.HEADER_SYMBOLS) == header_functions()
+
+
+def test_version_and_error_text_without_gpu(lib):
+    lib.dp_version.restype = ctypes.c_char_p
+    lib.dp_last_error.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.dp_version()
+    assert isinstance(lib.dp_last_error(), bytes)
+
+
+def test_host_validation_without_gpu(lib):
+    # offsets that are not strictly decreasing are rejected on the host,
+    # before any CUDA call
+    lib.sdp_solve.restype = ctypes.c_int
+    a = (ctypes.c_int32 * 3)(5, 5, 1)
+    rc = lib.sdp_solve(ctypes.c_void_p(1), ctypes.c_int64(100), a, 3, 0, None, None)
+    assert rc == 1  # DP_EINVAL
+    lib.dp_last_error.restype = ctypes.c_char_p
+    assert b"strictly decreasing" in lib.dp_last_error()
+    lib.mcm_solve.restype = ctypes.c_int
+    assert lib.mcm_solve(ctypes.c_void_p(1), 0, 0, ctypes.c_void_p(1), ctypes.c_void_p(1), None, None) == 1
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    from paper_2008_01938_gb300 import native
+    monkeypatch.setattr(native, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        native.load(str(tmp_path / "nope.so"))

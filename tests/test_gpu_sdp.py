@@ -1,0 +1,162 @@
+"""GPU parity for the simplified DP (Definition 1): the CUDA path through the
+C ABI against the CPU oracle, bit-exact, plus full-size closed forms and
+invariants."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_01938_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fullsize.json")
+M32 = (1 << 32) - 1
+
+
+@pytest.fixture(scope="module")
+def dp():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2008_01938_gb300 as dp
+    return dp
+
+
+def _gpu(dp, preset, n, offsets, op):
+    import torch
+    st = np.zeros(max(n, int(offsets[0])), dtype=np.uint32)
+    st[:offsets[0]] = np.asarray(preset, dtype=np.uint32)[:offsets[0]]
+    t = torch.from_numpy(st.view(np.int32)).cuda()
+    dp.sdp_solve(t, offsets, op=op, n=n)
+    dp.sync_status()
+    return t.cpu().numpy().view(np.uint32)[:n]
+
+
+CASES = [
+    # (n, k, amin, amax, seed): a_k >= 1024 (1024-wide steps), a_k small,
+    # single offset, k > 32 (offsets in shared memory), large a_1 (no ring)
+    (200000, 32, 1024, 8192, 1),
+    (50000, 8, 40, 700, 2),
+    (30000, 3, 1, 9, 3),
+    (12345, 1, 5, 5, 4),
+    (40000, 48, 100, 3000, 5),
+    (120000, 6, 20000, 40000, 6),
+    (3000, 5, 2000, 2999, 7),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("op", ["min", "add"])
+def test_parity_random(dp, case, op):
+    n, k, amin, amax, seed = case
+    inst = inputs.sdp_random(n=n, k=k, amin=amin, amax=amax, seed=seed)
+    got = _gpu(dp, inst.preset, n, inst.offsets, op)
+    ref = oracle.sdp(inst.preset, n, inst.offsets, op)
+    bad = np.flatnonzero(got != ref)
+    assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5].tolist()}"
+
+
+def test_consecutive_offsets_worst_case(dp):
+    # Section III-A, Fig. 4: a run of consecutive offsets makes the paper's
+    # pipeline threads collide; here it is just another offset set
+    offs = [40, 39, 38, 37, 36, 35, 10, 9, 8]
+    pre = inputs.SplitMix64(5).u32(40)
+    for op in ("min", "add"):
+        assert np.array_equal(_gpu(dp, pre, 100000, offs, op), oracle.sdp(pre, 100000, offs, op))
+
+
+def test_short_tables(dp):
+    for n in (0, 1, 5, 8, 9):
+        got = _gpu(dp, [3, 1, 4, 1, 5, 9, 2, 6], n, [8, 3], "add")
+        assert np.array_equal(got, oracle.sdp([3, 1, 4, 1, 5, 9, 2, 6], n, [8, 3], "add"))
+
+
+def fib_pair(i):
+    if i == 0:
+        return 0, 1
+    a, b = fib_pair(i >> 1)
+    c = (a * ((2 * b - a) & M32)) & M32
+    d = (a * a + b * b) & M32
+    return (d, (c + d) & M32) if i & 1 else (c, d)
+
+
+def test_fibonacci_full_length(dp):
+    n = 1 << 22
+    got = _gpu(dp, [0, 1], n, [2, 1], "add")
+    for i in [0, 1, 2, 3, 1000, 123456, n // 2, n - 2, n - 1]:
+        assert int(got[i]) == fib_pair(i)[0]
+    got1 = _gpu(dp, [1, 1], 4096, [2, 1], "add")   # the paper's preset: F(i+1)
+    assert all(int(got1[i]) == fib_pair(i + 1)[0] for i in (0, 1, 50, 4095))
+
+
+def _sha(a):
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+@pytest.mark.parametrize("op", ["min", "add"])
+def test_full_size_2p26(dp, op):
+    """2^26 cells, 32 offsets in [1024, 8192], uniform uint32 preset (seed 2):
+    whole-table SHA-256 against the oracle's, plus sampled values."""
+    if not os.path.exists(GOLDEN):
+        pytest.skip("golden file not generated")
+    g = json.load(open(GOLDEN))[f"sdp_n2p26_seed2_{op}"]
+    big = inputs.sdp_instance_big()
+    got = _gpu(dp, big.preset, big.n, big.offsets, op)
+    for i, v in g["samples"]:
+        assert int(got[i]) == v
+    assert _sha(got.astype("<u4")) == g["st_sha256"]
+
+
+def test_full_size_invariants(dp):
+    """Properties that hold at any size, checked on 2^24-cell GPU tables:
+    (+) is linear mod 2^32; (min) distributes over elementwise min, never
+    leaves the preset's values, and commutes with adding a constant."""
+    big = inputs.sdp_instance_big(n=1 << 24)
+    x = big.preset
+    y = inputs.SplitMix64(99).u32(x.size)
+    n, a = big.n, big.offsets
+    sx, sy = _gpu(dp, x, n, a, "add"), _gpu(dp, y, n, a, "add")
+    assert np.array_equal(_gpu(dp, (x + y).astype(np.uint32), n, a, "add"), (sx + sy).astype(np.uint32))
+    xs, ys = x >> np.uint32(1), y >> np.uint32(1)
+    mx, my = _gpu(dp, xs, n, a, "min"), _gpu(dp, ys, n, a, "min")
+    assert np.array_equal(_gpu(dp, np.minimum(xs, ys), n, a, "min"), np.minimum(mx, my))
+    assert np.isin(mx, xs).all()
+    assert np.array_equal(_gpu(dp, xs + np.uint32(7), n, a, "min"), mx + np.uint32(7))
+
+
+def test_host_entry_point(dp):
+    inst = inputs.sdp_random(n=70000, k=10, amin=300, amax=2000, seed=12)
+    st = np.zeros(inst.n, dtype=np.uint32)
+    st[:inst.offsets[0]] = inst.preset
+    dp.sdp_solve_host(st, inst.offsets, op="min")
+    assert np.array_equal(st, oracle.sdp(inst.preset, inst.n, inst.offsets, "min"))
+
+
+@pytest.mark.parametrize("op", ["min", "add"])
+def test_batched_parity(dp, op):
+    import torch
+    insts = [inputs.sdp_random(n=int(n), k=int(k), amin=16, amax=amax, seed=40 + i)
+             for i, (n, k, amax) in enumerate([(5000, 4, 100), (70000, 16, 4096), (1, 3, 50), (33333, 1, 64),
+                                               (200000, 20, 2000), (9000, 40, 900)])]
+    ns = [x.n for x in insts]
+    offs = [x.offsets for x in insts]
+    st_off = np.zeros(len(insts), dtype=np.int64)
+    tot = 0
+    for i, x in enumerate(insts):
+        st_off[i] = tot
+        tot += max(x.n, int(x.offsets[0]))
+    host = np.zeros(tot, dtype=np.uint32)
+    for i, x in enumerate(insts):
+        host[st_off[i]:st_off[i] + x.offsets[0]] = x.preset
+    t = torch.from_numpy(host.view(np.int32)).cuda()
+    plan = dp.SdpPlan(ns, offs, op=op)
+    plan.solve(t, torch.from_numpy(st_off).cuda())
+    dp.sync_status()
+    got = t.cpu().numpy().view(np.uint32)
+    for i, x in enumerate(insts):
+        ref = oracle.sdp(x.preset, x.n, x.offsets, op)
+        assert np.array_equal(got[st_off[i]:st_off[i] + x.n], ref), i
+    plan.destroy()
