@@ -1,0 +1,498 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MCM / S-DP solvers.
+
+Headline (one step = one solve of the whole MCM hot path): the 4096-matrix
+chain with dims uniform in [1, 32] (seed 1), int32 costs, int16 split table,
+one mcm_solve call per step with inputs resident in device memory; the metric
+is split evaluations per second, (n^3 - n) / 6 of them per solve.  L2 is
+flushed (a 256 MiB write) between timed steps, outside the timed events.
+
+Also printed in the same JSON line:
+  e2e          the same solve through mcm_solve_host (host buffers; the copy
+               of p in and of m and s out are inside the timed region);
+  roofline     the MCM kernel's INT32 issue rate against the ALU peak
+               (152 SMs x 128 INT32 lanes/clk x clock; 3 integer ops per
+               split evaluation), from CUDA events around each launch;
+  cpu_baseline the CPU oracle (single thread) on a bounded sample;
+  sdp          the 2^26-cell S-DP table, 32 offsets in [1024, 8192] (seed 2),
+               both operators: cells/s and HBM GB/s;
+  batched      10,000 chains, n log-uniform in [8, 512], dims U[1, 1000], int64
+               (seed 3): one graph-captured persistent launch vs a plain loop
+               of one mcm_solve per chain;
+  serve        a Poisson request trace (80 % MCM n in [16, 2048] int64, 20 %
+               S-DP n in [2^16, 2^24], 16 offsets in [64, 4096], min) through
+               the continuous-batching server: p50 / p99 latency and
+               throughput vs a plain sequential solve loop.
+
+--impl reference times the CPU oracle (the only reference this project has)
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_MCM = 4096
+EVALS_4096 = (N_MCM ** 3 - N_MCM) // 6
+METRIC = "MCM split-evals/s (n=4096, batched) vs plain; S-DP cells/s; served p99 latency"
+INT_OPS_PER_EVAL = 3          # weight multiply-add, second add, min
+INT32_LANES_PER_SM_CLK = 128  # 4 SMSPs x 32 lanes of integer issue per clock
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def _rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---------------------------------------------------------------------------
+# clock sampling (nvidia-smi during the timed region)
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, samples = [], [], set(), 0
+        for ts, line in self.lines:
+            if not (t0 - 0.15 <= ts <= t1 + 0.15):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            samples += 1
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                pass
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                                 parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": samples}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def _kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ["mcm.cu", "mcm_kernels.cuh", "dp_common.cuh"]:
+        h.update(open(os.path.join(ROOT, "paper_2008_01938_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic():
+    """DRAM bytes per launch of the MCM kernel from the committed ncu summary,
+    valid only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "mcm_main_n4096.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    msha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    mbytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not msha or not mbytes or msha.group(1) != _kernel_source_sha():
+        return None
+    return float(mbytes.group(1))
+
+
+def _cpu_baseline(n_sample=2048):
+    import oracle
+    from paper_2008_01938_gb300 import inputs
+    p = inputs.mcm_big()[: n_sample + 1]
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.mcm(p)
+    dt = time.perf_counter() - t0
+    ev = (n_sample ** 3 - n_sample) // 6
+    return {"value": ev / dt, "unit": "split-evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n_sample} matrices of the 4096-matrix chain ({ev} split-evals), "
+                      f"single-threaded C oracle, {dt:.2f} s"}
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2008_01938_gb300 as dp
+    from paper_2008_01938_gb300 import inputs, native
+    lib = native.load()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p_h = inputs.mcm_big()
+    p = torch.from_numpy(p_h).to(dev)
+    m = torch.empty((N_MCM, N_MCM), dtype=torch.int32, device=dev)
+    s = torch.empty((N_MCM, N_MCM), dtype=torch.int16, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        dp.mcm_solve(p, "i32", m, s)
+    dp.sync_status()
+
+    sampler = ClockSampler(local)
+    barrier()
+    t_wall0 = time.time()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    lib.dp_profile_begin()
+    for i in range(args.steps):
+        flush.fill_(i)
+        starts[i].record(stream)
+        dp.mcm_solve(p, "i32", m, s)
+        ends[i].record(stream)
+    barrier()
+    kms, kn, sms_, sn = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+    native.check(lib.dp_profile_end(ctypes.byref(kms), ctypes.byref(kn), ctypes.byref(sms_), ctypes.byref(sn)))
+    t_wall1 = time.time()
+    dp.sync_status()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    clocks = sampler.stop(t_wall0, t_wall1)
+    value = world * EVALS_4096 / (ms / 1e3)
+    kernel_ms = kms.value / max(kn.value, 1)
+
+    # correctness spot check of the timed output (cheap: final cell + digest)
+    gold = os.path.join(ROOT, "tests", "golden", "fullsize.json")
+    parity = None
+    if os.path.exists(gold):
+        g = json.load(open(gold))["mcm_n4096_seed1"]
+        mh = m.cpu().numpy()
+        parity = hashlib.sha256(mh.astype("<i4").tobytes()).hexdigest() == g["m_sha256"]
+
+    # e2e through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        ph = torch.from_numpy(p_h).pin_memory()
+        mh_t = torch.empty((N_MCM, N_MCM), dtype=torch.int32).pin_memory()
+        sh_t = torch.empty((N_MCM, N_MCM), dtype=torch.int16).pin_memory()
+        sp = ctypes.c_void_p(stream.cuda_stream)
+        native.check(lib.mcm_solve_host(ctypes.c_void_p(ph.data_ptr()), N_MCM, native.DP_COST_I32,
+                                        ctypes.c_void_p(mh_t.data_ptr()), ctypes.c_void_p(sh_t.data_ptr()), sp))
+        e2e_steps = max(3, min(args.steps, 20))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            flush.fill_(1)
+            native.check(lib.mcm_solve_host(ctypes.c_void_p(ph.data_ptr()), N_MCM, native.DP_COST_I32,
+                                            ctypes.c_void_p(mh_t.data_ptr()), ctypes.c_void_p(sh_t.data_ptr()), sp))
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * EVALS_4096 / e2e_s, "unit": "split-evals/s",
+               "h2d_bytes_per_step": (N_MCM + 1) * 4, "d2h_bytes_per_step": N_MCM * N_MCM * (4 + 2),
+               "ms_per_step": e2e_s * 1e3, "note": "includes the 256 MiB L2 flush write per step"}
+
+    peak = SM_COUNT * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = INT_OPS_PER_EVAL * EVALS_4096 / (kernel_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s (INT32)",
+            "frac": round(achieved / peak, 4), "traffic": _profile_traffic(),
+            "kernel": "mcm_main_kernel<int32>", "kernel_ms": round(kernel_ms, 4),
+            "peak_basis": "152 SMs x 128 INT32 lanes/clk x 2070 MHz (derived, not measured)"}
+    if clocks.get("sm_mhz"):
+        pk2 = SM_COUNT * INT32_LANES_PER_SM_CLK * clocks["sm_mhz"] * 1e6 / 1e12
+        roof["frac_at_run_clock"] = round(achieved / pk2, 4)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "split-evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "MCM n=4096 chain, dims U[1,32] seed 1, int32 m + int16 s, one mcm_solve per step",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks, "e2e": e2e, "roofline": roof, "parity_sha256_ok": parity,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = _cpu_baseline()
+    if world == 1 and not args.no_extras:
+        out["sdp"] = bench_sdp(dp, native, lib, dev, args)
+        out["batched"] = bench_batched(dp, native, lib, dev, args)
+        out["serve"] = bench_serve(dp, native, dev, args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def bench_sdp(dp, native, lib, dev, args):
+    import numpy as np
+    import torch
+    from paper_2008_01938_gb300 import inputs
+    big = inputs.sdp_instance_big()
+    a1 = int(big.offsets[0])
+    res = {"workload": "S-DP n=2^26 uint32, k=32 offsets in [1024,8192] (a_1=8192, a_k=1024), preset seed 2"}
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6683.8) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6683.8
+    st0 = np.zeros(big.n, dtype=np.uint32)
+    st0[:a1] = big.preset
+    t = torch.from_numpy(st0.view(np.int32)).to(dev)
+    for op in ("min", "add"):
+        dp.sdp_solve(t, big.offsets, op=op)
+        dp.sync_status()
+        reps = 3
+        lib.dp_profile_begin()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            dp.sdp_solve(t, big.offsets, op=op)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / reps
+        a, b, c, d = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+        native.check(lib.dp_profile_end(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+        kms = c.value / max(d.value, 1)
+        cells = big.n - a1
+        bytes_ = 4 * cells + 4 * a1
+        res[op] = {"cells_per_s": cells / (kms / 1e3), "kernel_ms": kms, "wall_ms": wall * 1e3,
+                   "roofline": {"bound": "hbm", "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm,
+                                "unit": "GB/s", "frac": bytes_ / (kms / 1e3) / 1e9 / hbm,
+                                "note": "dependency chain of (n-a_1)/a_k steps bounds it, not HBM"}}
+    return res
+
+
+def bench_batched(dp, native, lib, dev, args):
+    import numpy as np
+    import torch
+    from paper_2008_01938_gb300 import inputs
+    b = inputs.mcm_batch()
+    total = int(sum((int(n) ** 3 - int(n)) // 6 for n in b.ns))
+    plan = dp.McmPlan(b.ns, cost="i64")
+    p_all = torch.from_numpy(b.p_all).to(dev)
+    p_off = torch.from_numpy(b.p_off[:-1].copy()).to(dev)
+    tab_off = torch.from_numpy(b.tab_off[:-1].copy()).to(dev)
+    m_all = torch.empty(int(b.tab_off[-1]), dtype=torch.int64, device=dev)
+    s_all = torch.empty(int(b.tab_off[-1]), dtype=torch.int16, device=dev)
+    st = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(st):
+        plan.solve(p_all, p_off, tab_off, m_all, s_all, stream=st)
+    st.synchronize()
+    dp.sync_status()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        plan.solve(p_all, p_off, tab_off, m_all, s_all, stream=st)
+    reps = 3
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    dp.sync_status()
+    t_graph = e0.elapsed_time(e1) / reps / 1e3
+    gold = os.path.join(ROOT, "tests", "golden", "fullsize.json")
+    parity = None
+    if os.path.exists(gold):
+        gg = json.load(open(gold)).get("mcm_batch10000_seed3")
+        if gg:
+            parity = hashlib.sha256(m_all.cpu().numpy().astype("<i8").tobytes()).hexdigest() == gg["m_sha256_concat"]
+    # plain loop: one mcm_solve per chain, same device buffers
+    views = [(p_all[int(b.p_off[i]):int(b.p_off[i + 1])], m_all[int(b.tab_off[i]):int(b.tab_off[i + 1])].view(
+        int(b.ns[i]), int(b.ns[i])), s_all[int(b.tab_off[i]):int(b.tab_off[i + 1])].view(int(b.ns[i]), int(b.ns[i])))
+        for i in range(b.ns.size)]
+    for v in views[:50]:
+        dp.mcm_solve(v[0], "i64", v[1], v[2])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record()
+    for v in views:
+        dp.mcm_solve(v[0], "i64", v[1], v[2])
+    e1.record()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
+    dp.sync_status()
+    plan.destroy()
+    return {"workload": "10,000 chains, n log-uniform [8,512], dims U[1,1000] seed 3, int64 costs",
+            "split_evals": total, "graph_evals_per_s": total / t_graph, "graph_ms": t_graph * 1e3,
+            "plain_loop_evals_per_s": total / t_plain, "plain_loop_ms": t_plain * 1e3,
+            "speedup_vs_plain": t_plain / t_graph, "parity_sha256_ok": parity}
+
+
+def bench_serve(dp, native, dev, args):
+    import numpy as np
+    import torch
+    from paper_2008_01938_gb300 import inputs
+    trace = inputs.serve_trace(rate=args.serve_rate, duration=args.serve_seconds, seed=4)
+    if not trace:
+        return None
+    srv = dp.Server(hbm_cap_bytes=150 << 30, max_inflight=100000, num_streams=4, max_batch=64, device=dev.index)
+    # warm the kernels
+    for r in trace[:8]:
+        tk = srv.submit_mcm(r.dims) if r.kind == "mcm" else srv.submit_sdp(r.n, r.offsets, r.preset)
+        while srv.poll(tk) is None:
+            time.sleep(1e-4)
+        srv.release(tk)
+    t_base = srv.now() + 0.01
+    outstanding = {}
+    lat = []
+    busy = 0
+    i = 0
+    while i < len(trace) or outstanding:
+        now = srv.now()
+        while i < len(trace) and t_base + trace[i].t_arrival <= now:
+            r = trace[i]
+            tk = srv.submit_mcm(r.dims) if r.kind == "mcm" else srv.submit_sdp(r.n, r.offsets, r.preset)
+            if tk is None:
+                busy += 1
+                break
+            outstanding[tk] = t_base + r.t_arrival
+            i += 1
+        for tk in list(outstanding):
+            res = srv.poll(tk)
+            if res is not None:
+                if res.status != 0:
+                    raise RuntimeError(f"request failed with status {res.status}")
+                lat.append(res.t_done - outstanding.pop(tk))
+                srv.release(tk)
+        time.sleep(2e-5)
+    t_end = srv.now()
+    srv.close()
+    lat_ms = np.array(lat) * 1e3
+    served = {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+              "max_ms": float(lat_ms.max()), "requests": len(lat),
+              "throughput_req_s": len(lat) / (t_end - t_base), "busy_retries": busy}
+    # plain sequential solve loop over the same trace (service times measured,
+    # queueing simulated in arrival order)
+    svc = []
+    sub = trace[: min(len(trace), 500)]
+    for r in sub:
+        t0 = time.perf_counter()
+        if r.kind == "mcm":
+            pt = torch.from_numpy(r.dims).to(dev)
+            dp.mcm_solve(pt, "i64")
+        else:
+            st = np.zeros(max(r.n, int(r.offsets[0])), dtype=np.uint32)
+            st[: r.offsets[0]] = r.preset
+            tt = torch.from_numpy(st.view(np.int32)).to(dev)
+            dp.sdp_solve(tt, r.offsets, op="min", n=r.n)
+        dp.sync_status()
+        svc.append(time.perf_counter() - t0)
+    fin, lats = 0.0, []
+    for r, sv in zip(sub, svc):
+        start = max(r.t_arrival, fin)
+        fin = start + sv
+        lats.append(fin - r.t_arrival)
+    lats = np.array(lats) * 1e3
+    plain = {"p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
+             "requests": len(sub), "throughput_req_s": len(sub) / fin if fin > 0 else None}
+    return {"workload": f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s (seed 4): 80% MCM "
+                        f"n log-U[16,2048] int64, 20% S-DP n log-U[2^16,2^24] k=16 min; cap 150 GB",
+            "served": served, "plain_sequential_loop": plain}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, local = _rank()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2008_01938_gb300 import inputs
+    oracle.build()
+    n_s = 384
+    p = inputs.mcm_big()[: n_s + 1]
+    ev = (n_s ** 3 - n_s) // 6
+    for _ in range(args.warmup):
+        oracle.mcm(p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.mcm(p)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = ev / dt
+    sample = f"first {n_s} matrices of the 4096-matrix chain ({ev} split-evals) per step, single-threaded C oracle"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "split-evals/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": "MCM n=4096 chain, dims U[1,32] seed 1 (bounded sample per step)"},
+           "cpu_baseline": {"value": value, "unit": "split-evals/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "split-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -71,6 +71,15 @@ const char *dp_version(void);
  * the stream itself failed. */
 dp_status dp_sync_status(void *stream, int32_t *status_dev);
 
+/* Kernel timing.  Between dp_profile_begin() and dp_profile_end(), every
+ * launch of a solver kernel (not the small set-up kernels) made by this
+ * process is bracketed by two CUDA events recorded on the launching stream.
+ * dp_profile_end() waits for them and returns the summed device time in
+ * milliseconds and the number of launches for the MCM kernel (mcm_*) and the
+ * S-DP kernel (sdp_*).  Do not profile while capturing a CUDA graph. */
+dp_status dp_profile_begin(void);
+dp_status dp_profile_end(double *mcm_ms, int64_t *mcm_launches, double *sdp_ms, int64_t *sdp_launches);
+
 /* ------------------------------------------------------------------------- */
 /* MCM (Section IV-A, Eq. (2))                                                */
 /* ------------------------------------------------------------------------- */

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -48,6 +49,36 @@ long long spin_limit() {
     if (v > 0) return v;
   }
   return 1ll << 32;  // about two seconds of SM clock
+}
+
+namespace {
+std::atomic<bool> g_prof{false};
+std::mutex g_prof_mu;
+struct ProfPair {
+  int which;
+  cudaEvent_t a, b;
+};
+std::vector<ProfPair> g_prof_ev;
+}  // namespace
+
+bool profiling() { return g_prof.load(std::memory_order_relaxed); }
+
+void profile_mark(int which, cudaStream_t st, bool after) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!after) {
+    ProfPair p{which, nullptr, nullptr};
+    cudaEventCreate(&p.a);
+    cudaEventCreate(&p.b);
+    cudaEventRecord(p.a, st);
+    g_prof_ev.push_back(p);
+  } else {
+    for (auto it = g_prof_ev.rbegin(); it != g_prof_ev.rend(); ++it) {
+      if (it->which == which) {
+        cudaEventRecord(it->b, st);
+        break;
+      }
+    }
+  }
 }
 
 dp_status current_dev(DevState** out) {
@@ -270,8 +301,11 @@ dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const i
   if ((e = dpk::launch_mcm_prologue(a, sp.i64, st)) != cudaSuccess) return fail_cuda(e, "launch MCM prologue");
   const int c = sp.i64 ? 1 : 0;
   const int grid = (int)std::min<int64_t>((int64_t)ds->sms * ds->occ[c], (int64_t)sp.tasks.size());
+  const bool prof = profiling();
+  if (prof) profile_mark(0, st, false);
   if ((e = dpk::launch_mcm_main(a, sp.i64, std::max(grid, 1), st)) != cudaSuccess)
     return fail_cuda(e, "launch MCM kernel");
+  if (prof) profile_mark(0, st, true);
   return DP_OK;
 }
 
@@ -376,6 +410,41 @@ extern "C" {
 const char* dp_last_error(void) { return t_err.c_str(); }
 
 const char* dp_version(void) { return "dpgpu 0.1 (sm_103a)"; }
+
+dp_status dp_profile_begin(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& p : g_prof_ev) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_prof_ev.clear();
+  g_prof.store(true);
+  return DP_OK;
+}
+
+dp_status dp_profile_end(double* mcm_ms, int64_t* mcm_launches, double* sdp_ms, int64_t* sdp_launches) {
+  g_prof.store(false);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  double ms[2] = {0, 0};
+  int64_t cnt[2] = {0, 0};
+  dp_status rc = DP_OK;
+  for (auto& p : g_prof_ev) {
+    float t = 0;
+    cudaError_t e = cudaEventSynchronize(p.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p.a, p.b);
+    if (e != cudaSuccess && rc == DP_OK) rc = fail_cuda(e, "dp_profile_end");
+    ms[p.which] += t;
+    cnt[p.which] += 1;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_prof_ev.clear();
+  if (mcm_ms) *mcm_ms = ms[0];
+  if (mcm_launches) *mcm_launches = cnt[0];
+  if (sdp_ms) *sdp_ms = ms[1];
+  if (sdp_launches) *sdp_launches = cnt[1];
+  return rc;
+}
 
 dp_status dp_sync_status(void* stream, int32_t* status_dev) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -510,7 +579,10 @@ dp_status sdp_solve(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, dp_op 
   sdp_shape(a[0], a[k - 1], &args.threads, &args.ring_log2);
   args.status = status_dev ? status_dev : ds->status;
   for (int j = 0; j < k; ++j) args.one_offs[j] = a[j];
+  const bool prof = profiling();
+  if (prof) profile_mark(1, static_cast<cudaStream_t>(stream), false);
   cudaError_t e = dpk::launch_sdp(args, static_cast<cudaStream_t>(stream));
+  if (prof) profile_mark(1, static_cast<cudaStream_t>(stream), true);
   if (e != cudaSuccess) return fail_cuda(e, "sdp_solve: launch");
   return DP_OK;
 }
@@ -612,7 +684,10 @@ dp_status sdp_solve_batched(void* plan, uint32_t* ST_all, const int64_t* st_off,
   args.st_all = ST_all;
   args.st_off = st_off;
   args.status = status_dev ? status_dev : ds->status;
+  const bool prof = profiling();
+  if (prof) profile_mark(1, static_cast<cudaStream_t>(stream), false);
   cudaError_t e = dpk::launch_sdp(args, static_cast<cudaStream_t>(stream));
+  if (prof) profile_mark(1, static_cast<cudaStream_t>(stream), true);
   if (e != cudaSuccess) return fail_cuda(e, "sdp_solve_batched: launch");
   return DP_OK;
 }

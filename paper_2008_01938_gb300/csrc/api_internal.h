@@ -30,6 +30,11 @@ dp_status current_dev(DevState** out);
 
 long long spin_limit();     // bounded-wait budget in clock cycles
 
+// Kernel timing (dp_profile_begin / dp_profile_end): when enabled, the
+// launchers bracket each solver kernel with events on its stream.
+bool profiling();
+void profile_mark(int which, cudaStream_t st, bool after);  // which: 0 = MCM, 1 = S-DP
+
 // ---------------------------------------------------------------------------
 // MCM plans
 // ---------------------------------------------------------------------------
