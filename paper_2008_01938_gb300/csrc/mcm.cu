@@ -23,7 +23,9 @@ __device__ __forceinline__ int64_t tile_index(const McmInstDev& in, int I, int J
   return in.tile_base + (int64_t)I * in.nt - (int64_t)I * (I - 1) / 2 + (J - I);
 }
 
-// Shared-memory carve-up (byte offsets); identical for all blocks.
+// Shared-memory carve-up (byte offsets); identical for all blocks.  During a
+// finisher's in-tile solve the bulk-copy stages are idle (every copy of the
+// task has landed), so the solve's working arrays are carved from them.
 template <bool I64>
 struct Smem {
   static constexpr int ES = I64 ? 8 : 4;
@@ -39,10 +41,19 @@ struct Smem {
   static constexpr int FINPKI = FINPP + 128;                     // p[32I+1 ..] << S
   static constexpr int FINPKJ = FINPKI + 128;                    // p[32J+1 ..] << S
   static constexpr int FINACC = FINPKJ + 128;                    // bulk-task partial minima
-  static constexpr int BEST = FINACC + T * T * 8;                // merged segment minima
-  static constexpr int UT = BEST + T * T * 8;                    // unpacked U, transposed, pitch 36
-  static constexpr int XV = UT + T * 36 * ES;                    // final values of the tile
-  static constexpr int TOTAL = XV + T * T * ES;
+  static constexpr int BEST = FINACC + T * T * 8;                // running (value, k) keys
+  static constexpr int TOTAL = BEST + T * T * 8;
+  // in-tile solve arrays, inside the stage area (pitch 32 everywhere: the
+  // access patterns of the pipelined solve are bank-conflict free with it)
+  static constexpr int UP = 36;                                  // pitch of U^T (bank-conflict free)
+  static constexpr int LP = 40;                                  // pitch of L
+  static constexpr int XP = 33;                                  // pitch of X and of the minima
+  static constexpr int UT = STA;                                 // U^T[t][li] = m[IT+li][IT+t]
+  static constexpr int LM = UT + ((T * UP * ES + 127) / 128) * 128;  // L[u][lj] = m[JT+u+1][JT+lj]
+  static constexpr int XV = LM + ((T * LP * ES + 127) / 128) * 128;  // final values of the tile
+  static constexpr int ACCV = XV + ((T * XP * ES + 127) / 128) * 128;  // running minima of older splits
+  static constexpr int PV = ACCV + ((T * XP * ES + 127) / 128) * 128;  // p[IT+li], p[IT+t+1], p[JT+u+1]
+  static_assert(PV + 3 * T * ES <= STPK, "in-tile arrays must fit in the stage area");
 };
 
 __device__ __forceinline__ void bar_compute() {  // the 256 compute threads only
@@ -67,6 +78,150 @@ __device__ __forceinline__ bool bar_compute_and(bool v) {
 
 template <typename E>
 __device__ __forceinline__ E umin(E a, E b) { return a < b ? a : b; }
+
+// ---------------------------------------------------------------------------
+// In-tile solve of an off-diagonal tile (I, J).
+// X is the tile; its in-tile splits are
+//   column splits k = IT + t, li <= t <= 30:  U[li][t] + X[t+1][lj] + w
+//   row splits    k = JT + u,  0 <= u < lj:   X[li][u] + L[u][lj] + w
+// with U = the diagonal tile (I, I), L = rows shifted by one of (J, J) and
+// w = p[IT+li] p[k+1] p[JT+lj+1].
+// The tile is cut into 4 x 4 blocks of 8 x 8; block (bi, bj) depends on the
+// blocks below it in its column and left of it in its row.  Blocks are solved
+// one block-diagonal E = bj - bi at a time (7 steps), one warp per block:
+//   * the warp first folds in the splits whose operand lies in the two
+//     neighbour blocks finished in the previous step (8x8x8 products);
+//   * then it runs the paper's diagonal-order wavefront over the block's 15
+//     cell diagonals with warp shuffles only (lane = column c + 8 g, cells of
+//     rows g and g + 4);
+//   * warps without a block in this step fold the previous step's blocks into
+//     the blocks two or more diagonals ahead.
+// Only values are carried; the split index is recovered after the tile is
+// published.
+// ---------------------------------------------------------------------------
+template <typename E>
+struct BlkView {
+  E* Xv;          // X[li * XP + lj] final values
+  E* acc;         // running minima of the splits folded so far, same layout
+  const E* Ut;    // Ut[t * UP + li] = U[li][t]
+  const E* Lm;    // Lm[u * LP + lj] = L[u][lj]
+  const E* pI;    // p[IT + li]
+  const E* pI1;   // p[IT + t + 1]
+  const E* pJ1;   // p[JT + u + 1]
+  int UP, LP, XP;
+};
+
+// Column splits of the lane's two cells (rows R + g, R + g + 4, column C + c)
+// whose second operand lies in block row si (rows 8si .. 8si+7).
+template <typename E>
+__device__ __forceinline__ void blk_col_product(const BlkView<E>& v, int R, int C, int si, int g, int c, E w0,
+                                                E w1, E& m0, E& m1) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int t = 8 * si - 1 + q;
+    const E x = v.Xv[(t + 1) * v.XP + C + c];
+    const E pk = v.pI1[t];
+    m0 = umin(m0, v.Ut[t * v.UP + R + g] + x + w0 * pk);
+    m1 = umin(m1, v.Ut[t * v.UP + R + g + 4] + x + w1 * pk);
+  }
+}
+
+// Row splits of the lane's two cells whose first operand lies in block
+// column sj (columns 8sj .. 8sj+7).
+template <typename E>
+__device__ __forceinline__ void blk_row_product(const BlkView<E>& v, int R, int C, int sj, int g, int c, E w0,
+                                                E w1, E& m0, E& m1) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int u = 8 * sj + q;
+    const E l = v.Lm[u * v.LP + C + c];
+    const E pk = v.pJ1[u];
+    m0 = umin(m0, v.Xv[(R + g) * v.XP + u] + l + w0 * pk);
+    m1 = umin(m1, v.Xv[(R + g + 4) * v.XP + u] + l + w1 * pk);
+  }
+}
+
+// Wavefront over one 8x8 block (origin R0, C0) by one warp; v0 / v1 hold the
+// minima of all splits outside the block for the lane's two cells on entry
+// and the final values on exit (also stored to Xv).
+template <typename E>
+__device__ __forceinline__ void blk_solve8(const BlkView<E>& v, int R0, int C0, int g, int c, E w0, E w1, E& v0,
+                                           E& v1) {
+  const int r0 = g, r1 = g + 4;
+#pragma unroll
+  for (int e = -7; e <= 7; ++e) {
+    const E xe = (c - r0 == e) ? v0 : v1;  // this lane's cell on diagonal e, if any
+    const int a = c - e;                   // column split from row a of the block
+    const int ac = a < 1 ? 1 : (a > 7 ? 7 : a);
+    const E xa = __shfl_sync(0xffffffffu, xe, (ac & 3) * 8 + c);
+    const int b0 = r0 + e, b1 = r1 + e;    // row splits from columns b0, b1
+    const int b0c = b0 < 0 ? 0 : (b0 > 7 ? 7 : b0), b1c = b1 < 0 ? 0 : (b1 > 7 ? 7 : b1);
+    const E xb0 = __shfl_sync(0xffffffffu, xe, g * 8 + b0c);
+    const E xb1 = __shfl_sync(0xffffffffu, xe, g * 8 + b1c);
+    const int t = R0 + ac - 1;
+    const E pkt = v.pI1[t];
+    const E ca0 = v.Ut[t * v.UP + R0 + r0] + xa + w0 * pkt;
+    const E ca1 = v.Ut[t * v.UP + R0 + r1] + xa + w1 * pkt;
+    const E cb0 = xb0 + v.Lm[(C0 + b0c) * v.LP + C0 + c] + w0 * v.pJ1[C0 + b0c];
+    const E cb1 = xb1 + v.Lm[(C0 + b1c) * v.LP + C0 + c] + w1 * v.pJ1[C0 + b1c];
+    if (c - r0 > e) {
+      if (a <= 7) v0 = umin(v0, ca0);
+      if (b0 >= 0) v0 = umin(v0, cb0);
+    }
+    if (c - r1 > e) {
+      if (a <= 7) v1 = umin(v1, ca1);
+      if (b1 >= 0) v1 = umin(v1, cb1);
+    }
+  }
+  v.Xv[(R0 + r0) * v.XP + C0 + c] = v0;
+  v.Xv[(R0 + r1) * v.XP + C0 + c] = v1;
+}
+
+// The whole in-tile solve (all 8 compute warps; ends with Xv final).
+template <typename E>
+__device__ __forceinline__ void tile_solve_blocks(const BlkView<E>& v, int warp, int lane) {
+  const int g = lane >> 3, c = lane & 7;
+#pragma unroll 1
+  for (int s = 0; s < 7; ++s) {
+    const int E_ = s - 3;
+    const int nb = 4 - (E_ < 0 ? -E_ : E_);
+    const int bi0 = E_ < 0 ? -E_ : 0;
+    if (warp < nb) {
+      const int bi = bi0 + warp, bj = bi + E_;
+      const int R = 8 * bi, C = 8 * bj;
+      const E pj = v.pJ1[C + c];
+      const E w0 = v.pI[R + g] * pj, w1 = v.pI[R + g + 4] * pj;
+      E v0 = v.acc[(R + g) * v.XP + C + c];
+      E v1 = v.acc[(R + g + 4) * v.XP + C + c];
+      if (bi < 3) blk_col_product(v, R, C, bi + 1, g, c, w0, w1, v0, v1);  // block below, finished last step
+      if (bj > 0) blk_row_product(v, R, C, bj - 1, g, c, w0, w1, v0, v1);  // block to the left
+      blk_solve8(v, R, C, g, c, w0, w1, v0, v1);
+    } else if (s >= 1) {
+      // fold the blocks of diagonal E_-1 into the blocks on diagonals >= E_+1
+      const int idle = warp - nb, nidle = 8 - nb;
+      const int Es = E_ - 1;
+      int k = 0;
+      for (int blk = 0; blk < 16; ++blk) {
+        const int ti = blk >> 2, tj = blk & 3;
+        if (tj - ti < E_ + 1) continue;
+        const int si = tj - Es, sj = ti + Es;
+        const bool hc = si > ti && si <= 3, hr = sj >= 0 && sj < tj;
+        if (!hc && !hr) continue;
+        if ((k++ % nidle) != idle) continue;
+        const int R = 8 * ti, C = 8 * tj;
+        const E pj = v.pJ1[C + c];
+        const E w0 = v.pI[R + g] * pj, w1 = v.pI[R + g + 4] * pj;
+        E m0 = v.acc[(R + g) * v.XP + C + c];
+        E m1 = v.acc[(R + g + 4) * v.XP + C + c];
+        if (hc) blk_col_product(v, R, C, si, g, c, w0, w1, m0, m1);
+        if (hr) blk_row_product(v, R, C, sj, g, c, w0, w1, m0, m1);
+        v.acc[(R + g) * v.XP + C + c] = m0;
+        v.acc[(R + g + 4) * v.XP + C + c] = m1;
+      }
+    }
+    bar_compute();
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Bulk segment reductions (one compute group, 128 threads, 4 x 2 cells each).
@@ -144,7 +299,7 @@ __device__ __forceinline__ void for_each_segment(const McmTask& t, F&& body) {
 }
 
 template <bool I64>
-__global__ void __launch_bounds__(kMcmThreads) mcm_main_kernel(const McmLaunchArgs a) {
+__global__ void __launch_bounds__(kMcmThreads, 3) mcm_main_kernel(const McmLaunchArgs a) {
   using E = typename Cost<I64>::E;
   constexpr int KB = Cost<I64>::KB;
   using SM = Smem<I64>;
@@ -164,8 +319,7 @@ __global__ void __launch_bounds__(kMcmThreads) mcm_main_kernel(const McmLaunchAr
   uint32_t* finPKJ = reinterpret_cast<uint32_t*>(smem + SM::FINPKJ);
   unsigned long long* finAcc = reinterpret_cast<unsigned long long*>(smem + SM::FINACC);
   unsigned long long* bestS = reinterpret_cast<unsigned long long*>(smem + SM::BEST);
-  E* Ut = reinterpret_cast<E*>(smem + SM::UT);
-  E* Xv = reinterpret_cast<E*>(smem + SM::XV);
+  E* Xv = reinterpret_cast<E*>(smem + SM::XV);  // in-tile solve only (stage area)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -212,6 +366,9 @@ __global__ void __launch_bounds__(kMcmThreads) mcm_main_kernel(const McmLaunchAr
     if (warp == kComputeThreads / 32) {
       // ===================== producer warp (lane 0) =====================
       if (lane == 0) {
+        // the stage area was written and read through the generic proxy by the
+        // previous task's in-tile solve; order that before this task's copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         bool ok = true;
         bool issued[2][kStages] = {{false, false}, {false, false}};
         bool fin_issued = false;
@@ -368,54 +525,109 @@ __global__ void __launch_bounds__(kMcmThreads) mcm_main_kernel(const McmLaunchAr
             if (task.nparts > 0) cb[r] = umin(cb[r], finAcc[li * T + lane]);
           }
           if (D >= 1) {
+            E* Ut = reinterpret_cast<E*>(smem + SM::UT);
+            E* Lm = reinterpret_cast<E*>(smem + SM::LM);
+            E* accv = reinterpret_cast<E*>(smem + SM::ACCV);
+            E* pv = reinterpret_cast<E*>(smem + SM::PV);
             for (int idx = tid; idx < T * T; idx += kComputeThreads) {
-              const int t = idx >> 5, li = idx & 31;
-              Ut[t * 36 + li] = finU[t * T + li] >> shiftv;
+              const int t = idx >> 5, x = idx & 31;
+              Ut[t * SM::UP + x] = finU[idx] >> shiftv;
+              Lm[t * SM::LP + x] = finL[idx] >> shiftv;
+            }
+            if (tid < T) {
+              pv[tid] = (E)finPP[tid];
+              pv[T + tid] = (E)(finPKI[tid] >> shiftv);
+              pv[2 * T + tid] = (E)(finPKJ[tid] >> shiftv);
             }
             // boundary split k = IT + 31: U[li][31] + m[IT+32][j] + w
             const E brow = finBrow[lane] >> shiftv;
             const E pI32 = (E)(finPKI[T - 1] >> shiftv);
+            E bnd[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               const int li = 4 * w + r;
-              const E u = finU[(T - 1) * T + li] >> shiftv;
-              const E cand = u + brow + pi[r] * pI32 * pj1;
-              cb[r] = umin(cb[r], ((unsigned long long)cand << KB) | (unsigned)(IT + T - 1));
+              bestS[li * T + lane] = cb[r];  // external minimum: (value, smallest k)
+              bnd[r] = (finU[(T - 1) * T + li] >> shiftv) + brow + pi[r] * pI32 * pj1;
+              accv[li * SM::XP + lane] = umin((E)(cb[r] >> KB), bnd[r]);
             }
             bar_compute();
-#pragma unroll 1
-            for (int e = -(T - 1); e <= T - 1; ++e) {
+            {
+              const BlkView<E> bv{Xv, accv, Ut, Lm, pv, pv + T, pv + 2 * T, SM::UP, SM::LP, SM::XP};
+              tile_solve_blocks<E>(bv, warp, lane);
+            }
+            // ---------------- outputs needed by other tiles, then publish ----------------
+            const int64_t nn = n;
+            E vals[4];
 #pragma unroll
-              for (int r = 0; r < 4; ++r)
-                if (lane - (4 * w + r) == e) Xv[(4 * w + r) * T + lane] = (E)(cb[r] >> KB);
-              bar_compute();
-              // column push: source (aa, lane) on diagonal e, split k = IT + aa - 1
-              const int aa = lane - e;
-              if (aa >= 1 && aa <= T - 1 && 4 * w < aa) {
-                const E xa = Xv[aa * T + lane];
-                const E q = (E)(finPKI[aa - 1] >> shiftv) * pj1;
-                const unsigned kk = (unsigned)(IT + aa - 1);
+            for (int r = 0; r < 4; ++r) vals[r] = Xv[(4 * w + r) * SM::XP + lane];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                  if (4 * w + r < aa) {
-                    const E cand = Ut[(aa - 1) * 36 + 4 * w + r] + xa + pi[r] * q;
-                    cb[r] = umin(cb[r], ((unsigned long long)cand << KB) | kk);
-                  }
-                }
+            for (int r = 0; r < 4; ++r) {
+              const int li = 4 * w + r;
+              const int64_t i = IT + li, j = JT + lane;
+              if (i < nn && j < nn) {
+                if constexpr (I64)
+                  static_cast<int64_t*>(inst.m)[i * nn + j] = (int64_t)vals[r];
+                else
+                  static_cast<int32_t*>(inst.m)[i * nn + j] = (int32_t)vals[r];
               }
-              // row push: source (li, b) on diagonal e, split k = JT + b
+              const int64_t i2 = JT + li, j2 = IT + lane;  // mirror tile (J, I)
+              if (i2 < nn && j2 < nn) {
+                if constexpr (I64)
+                  static_cast<int64_t*>(inst.m)[i2 * nn + j2] = 0;
+                else
+                  static_cast<int32_t*>(inst.m)[i2 * nn + j2] = 0;
+                inst.s[i2 * nn + j2] = -1;
+              }
+            }
+            {
+              E* af = static_cast<E*>(a.af) + tidx * T * T;
+              E pa[4];
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                if constexpr (I64)
+                  pa[r] = ((E)vals[r] << 16) | (E)(JT + lane);
+                else
+                  pa[r] = (vals[r] << S) | (E)(lane & ((1 << (S < 5 ? S : 5)) - 1));
+              }
+              if constexpr (I64) {
+                *reinterpret_cast<ulonglong2*>(af + lane * T + 4 * w) = make_ulonglong2(pa[0], pa[1]);
+                *reinterpret_cast<ulonglong2*>(af + lane * T + 4 * w + 2) = make_ulonglong2(pa[2], pa[3]);
+              } else {
+                *reinterpret_cast<uint4*>(af + lane * T + 4 * w) = make_uint4(pa[0], pa[1], pa[2], pa[3]);
+              }
+              E* bf = static_cast<E*>(a.bf);
 #pragma unroll
               for (int r = 0; r < 4; ++r) {
                 const int li = 4 * w + r;
-                const int b = li + e;
-                if (b >= 0 && b < lane) {
-                  const E xb = Xv[li * T + b];
-                  const E lv = finL[b * T + lane] >> shiftv;
-                  const E wt = pi[r] * (E)(finPKJ[b] >> shiftv) * pj1;
-                  const E cand = xb + lv + wt;
-                  cb[r] = umin(cb[r], ((unsigned long long)cand << KB) | (unsigned)(JT + b));
-                }
+                const E pb = vals[r] << shiftv;
+                if (li >= 1)
+                  bf[tidx * T * T + (li - 1) * T + lane] = pb;
+                else if (I >= 1)
+                  bf[tile_index(inst, I - 1, J) * T * T + (T - 1) * T + lane] = pb;
               }
+            }
+            bar_compute();
+            if (tid == 0) {
+              __threadfence();
+              st_release(a.flags + tidx, 1);
+            }
+            // ---------------- split table: smallest k reaching the final value ----------------
+            // k order: column splits IT+li..IT+30 < boundary IT+31 < external splits < row splits JT+u
+            const unsigned long long kmask = (1ull << KB) - 1ull;
+#pragma unroll 1
+            for (int r = 0; r < 4; ++r) {
+              const int li = 4 * w + r;
+              const E v = vals[r];
+              const E w0 = pi[r] * pj1;
+              int k = -1;
+              for (int t = li; t <= T - 2 && k < 0; ++t)
+                if (Ut[t * SM::UP + li] + Xv[(t + 1) * SM::XP + lane] + w0 * pv[T + t] == v) k = IT + t;
+              if (k < 0 && bnd[r] == v) k = IT + T - 1;
+              if (k < 0 && (E)(bestS[li * T + lane] >> KB) == v) k = (int)(bestS[li * T + lane] & kmask);
+              for (int u = 0; u < lane && k < 0; ++u)
+                if (Xv[li * SM::XP + u] + Lm[u * SM::LP + lane] + w0 * pv[2 * T + u] == v) k = JT + u;
+              const int64_t i = IT + li, j = JT + lane;
+              if (i < nn && j < nn) inst.s[i * nn + j] = (int16_t)k;
             }
           } else {
             // diagonal tile: ordinary MCM on the 32-matrix sub-chain
@@ -446,7 +658,6 @@ __global__ void __launch_bounds__(kMcmThreads) mcm_main_kernel(const McmLaunchAr
                 }
               }
             }
-          }
           // ------------------ outputs ------------------
           const int64_t nn = n;
           const unsigned long long kmask = (1ull << KB) - 1ull;
@@ -504,6 +715,7 @@ __global__ void __launch_bounds__(kMcmThreads) mcm_main_kernel(const McmLaunchAr
             else if (I >= 1)
               bf[tile_index(inst, I - 1, J) * T * T + (T - 1) * T + lane] = pb;
           }
+          }
         }
       }
     }
@@ -511,10 +723,10 @@ __global__ void __launch_bounds__(kMcmThreads) mcm_main_kernel(const McmLaunchAr
     __syncthreads();
     if (tid == 0 && *reinterpret_cast<volatile int32_t*>(status) == 0) {
       __threadfence();
-      if (finisher)
-        st_release(a.flags + tidx, 1);
-      else
+      if (!finisher)
         red_release_add(a.counters + tidx, 1);
+      else if (D == 0)
+        st_release(a.flags + tidx, 1);  // off-diagonal tiles publish right after their values
     }
   }
 }
