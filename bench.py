@@ -265,7 +265,7 @@ def run_gb300(args):
         "config": {"workload": "MCM n=4096 chain, dims U[1,32] seed 1, int32 m + int16 s, one mcm_solve per step",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "clocks": clocks, "e2e": e2e, "roofline": roof, "parity_sha256_ok": parity,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -135,6 +135,8 @@ namespace {
 constexpr int kLevelsPerPart = 4;
 constexpr int kMinBulkLevels = 2;
 
+// Queue order: by the tile-diagonal at which a task becomes ready; within a
+// diagonal, finishers (the critical path) before bulk tasks.
 struct SortKey {
   int32_t bucket, kind, inst, I, J;
   bool operator<(const SortKey& o) const {
@@ -300,12 +302,14 @@ dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const i
   a.s_all = s_all;
   if ((e = dpk::launch_mcm_prologue(a, sp.i64, st)) != cudaSuccess) return fail_cuda(e, "launch MCM prologue");
   const int c = sp.i64 ? 1 : 0;
-  const int grid = (int)std::min<int64_t>((int64_t)ds->sms * ds->occ[c], (int64_t)sp.tasks.size());
+  const int grid = (int)std::max<int64_t>(2, std::min<int64_t>((int64_t)ds->sms * ds->occ[c], (int64_t)sp.tasks.size()));
   const bool prof = profiling();
   if (prof) profile_mark(0, st, false);
   if ((e = dpk::launch_mcm_main(a, sp.i64, std::max(grid, 1), st)) != cudaSuccess)
     return fail_cuda(e, "launch MCM kernel");
   if (prof) profile_mark(0, st, true);
+  if ((e = dpk::launch_mcm_splits(a, sp.i64, ds->sms * 8, st)) != cudaSuccess)
+    return fail_cuda(e, "launch MCM split pass");
   return DP_OK;
 }
 

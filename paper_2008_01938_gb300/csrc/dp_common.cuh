@@ -53,11 +53,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Waits for the phase of parity `parity` to complete; false on timeout.
+// After a few quick polls the waiting warp sleeps between polls, so blocks
+// that wait for data do not take issue slots from blocks that compute.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
+  uint32_t polls = 0, backoff = 32;
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > limit) return false;
+    if (++polls > 4) {
+      __nanosleep(backoff);
+      backoff = backoff < 512 ? backoff * 2 : 512;
+    }
   }
   return true;
 }

@@ -12,6 +12,9 @@ namespace dpk {
 namespace {
 
 constexpr int T = kTile;
+constexpr int kUP = 36;  // pitch of U^T in shared memory (bank-conflict free for the block solve)
+constexpr int kLP = 40;  // pitch of L
+constexpr int kXP = 33;  // pitch of X and of the running minima
 
 template <bool I64>
 struct Cost {
@@ -45,9 +48,7 @@ struct Smem {
   static constexpr int TOTAL = BEST + T * T * 8;
   // in-tile solve arrays, inside the stage area (pitch 32 everywhere: the
   // access patterns of the pipelined solve are bank-conflict free with it)
-  static constexpr int UP = 36;                                  // pitch of U^T (bank-conflict free)
-  static constexpr int LP = 40;                                  // pitch of L
-  static constexpr int XP = 33;                                  // pitch of X and of the minima
+  static constexpr int UP = kUP, LP = kLP, XP = kXP;
   static constexpr int UT = STA;                                 // U^T[t][li] = m[IT+li][IT+t]
   static constexpr int LM = UT + ((T * UP * ES + 127) / 128) * 128;  // L[u][lj] = m[JT+u+1][JT+lj]
   static constexpr int XV = LM + ((T * LP * ES + 127) / 128) * 128;  // final values of the tile
@@ -99,54 +100,47 @@ __device__ __forceinline__ E umin(E a, E b) { return a < b ? a : b; }
 // Only values are carried; the split index is recovered after the tile is
 // published.
 // ---------------------------------------------------------------------------
-template <typename E>
-struct BlkView {
-  E* Xv;          // X[li * XP + lj] final values
-  E* acc;         // running minima of the splits folded so far, same layout
-  const E* Ut;    // Ut[t * UP + li] = U[li][t]
-  const E* Lm;    // Lm[u * LP + lj] = L[u][lj]
-  const E* pI;    // p[IT + li]
-  const E* pI1;   // p[IT + t + 1]
-  const E* pJ1;   // p[JT + u + 1]
-  int UP, LP, XP;
-};
 
 // Column splits of the lane's two cells (rows R + g, R + g + 4, column C + c)
-// whose second operand lies in block row si (rows 8si .. 8si+7).
+// whose second operand lies in block row si (rows 8si .. 8si+7).  Pointers
+// are rebased so that the loop indexes with lane constants only:
+//   xs = Xv + (8si)*XP + C, us = Ut + (8si-1)*UP + R, ps = pI1 + 8si - 1.
 template <typename E>
-__device__ __forceinline__ void blk_col_product(const BlkView<E>& v, int R, int C, int si, int g, int c, E w0,
-                                                E w1, E& m0, E& m1) {
+__device__ __forceinline__ void blk_col_product(const E* __restrict__ xs, const E* __restrict__ us,
+                                                const E* __restrict__ ps, int g, int c, E w0, E w1, E& m0, E& m1) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const int t = 8 * si - 1 + q;
-    const E x = v.Xv[(t + 1) * v.XP + C + c];
-    const E pk = v.pI1[t];
-    m0 = umin(m0, v.Ut[t * v.UP + R + g] + x + w0 * pk);
-    m1 = umin(m1, v.Ut[t * v.UP + R + g + 4] + x + w1 * pk);
+    const E x = xs[q * kXP + c];
+    const E pk = ps[q];
+    m0 = umin(m0, us[q * kUP + g] + x + w0 * pk);
+    m1 = umin(m1, us[q * kUP + g + 4] + x + w1 * pk);
   }
 }
 
 // Row splits of the lane's two cells whose first operand lies in block
-// column sj (columns 8sj .. 8sj+7).
+// column sj (columns 8sj .. 8sj+7):
+//   xr = Xv + R*XP + 8sj, ls = Lm + (8sj)*LP + C, ps = pJ1 + 8sj.
 template <typename E>
-__device__ __forceinline__ void blk_row_product(const BlkView<E>& v, int R, int C, int sj, int g, int c, E w0,
-                                                E w1, E& m0, E& m1) {
+__device__ __forceinline__ void blk_row_product(const E* __restrict__ xr, const E* __restrict__ ls,
+                                                const E* __restrict__ ps, int g, int c, E w0, E w1, E& m0, E& m1) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const int u = 8 * sj + q;
-    const E l = v.Lm[u * v.LP + C + c];
-    const E pk = v.pJ1[u];
-    m0 = umin(m0, v.Xv[(R + g) * v.XP + u] + l + w0 * pk);
-    m1 = umin(m1, v.Xv[(R + g + 4) * v.XP + u] + l + w1 * pk);
+    const E l = ls[q * kLP + c];
+    const E pk = ps[q];
+    m0 = umin(m0, xr[g * kXP + q] + l + w0 * pk);
+    m1 = umin(m1, xr[(g + 4) * kXP + q] + l + w1 * pk);
   }
 }
 
 // Wavefront over one 8x8 block (origin R0, C0) by one warp; v0 / v1 hold the
 // minima of all splits outside the block for the lane's two cells on entry
-// and the final values on exit (also stored to Xv).
+// and the final values on exit (also stored to X).  Rebased pointers:
+//   xb = Xv + R0*XP + C0, ub = Ut + (R0-1)*UP + R0 (so ub[a*UP + r] = U[R0+r][R0+a-1]),
+//   lb = Lm + C0*LP + C0, pi1 = pI1 + R0 - 1, pj1 = pJ1 + C0.
 template <typename E>
-__device__ __forceinline__ void blk_solve8(const BlkView<E>& v, int R0, int C0, int g, int c, E w0, E w1, E& v0,
-                                           E& v1) {
+__device__ __forceinline__ void blk_solve8(E* __restrict__ xb, const E* __restrict__ ub, const E* __restrict__ lb,
+                                           const E* __restrict__ pi1, const E* __restrict__ pj1, int g, int c, E w0,
+                                           E w1, E& v0, E& v1) {
   const int r0 = g, r1 = g + 4;
 #pragma unroll
   for (int e = -7; e <= 7; ++e) {
@@ -158,12 +152,11 @@ __device__ __forceinline__ void blk_solve8(const BlkView<E>& v, int R0, int C0, 
     const int b0c = b0 < 0 ? 0 : (b0 > 7 ? 7 : b0), b1c = b1 < 0 ? 0 : (b1 > 7 ? 7 : b1);
     const E xb0 = __shfl_sync(0xffffffffu, xe, g * 8 + b0c);
     const E xb1 = __shfl_sync(0xffffffffu, xe, g * 8 + b1c);
-    const int t = R0 + ac - 1;
-    const E pkt = v.pI1[t];
-    const E ca0 = v.Ut[t * v.UP + R0 + r0] + xa + w0 * pkt;
-    const E ca1 = v.Ut[t * v.UP + R0 + r1] + xa + w1 * pkt;
-    const E cb0 = xb0 + v.Lm[(C0 + b0c) * v.LP + C0 + c] + w0 * v.pJ1[C0 + b0c];
-    const E cb1 = xb1 + v.Lm[(C0 + b1c) * v.LP + C0 + c] + w1 * v.pJ1[C0 + b1c];
+    const E pkt = pi1[ac];
+    const E ca0 = ub[ac * kUP + r0] + xa + w0 * pkt;
+    const E ca1 = ub[ac * kUP + r1] + xa + w1 * pkt;
+    const E cb0 = xb0 + lb[b0c * kLP + c] + w0 * pj1[b0c];
+    const E cb1 = xb1 + lb[b1c * kLP + c] + w1 * pj1[b1c];
     if (c - r0 > e) {
       if (a <= 7) v0 = umin(v0, ca0);
       if (b0 >= 0) v0 = umin(v0, cb0);
@@ -173,13 +166,27 @@ __device__ __forceinline__ void blk_solve8(const BlkView<E>& v, int R0, int C0, 
       if (b1 >= 0) v1 = umin(v1, cb1);
     }
   }
-  v.Xv[(R0 + r0) * v.XP + C0 + c] = v0;
-  v.Xv[(R0 + r1) * v.XP + C0 + c] = v1;
+  xb[r0 * kXP + c] = v0;
+  xb[r1 * kXP + c] = v1;
+}
+
+// Folds into block (ti, tj) the splits whose operand lies in block (si, tj)
+// below it (hc) and / or block (ti, sj) left of it (hr); m0 / m1 in/out.
+template <typename E>
+__device__ __forceinline__ void blk_fold(const E* __restrict__ Xv, const E* __restrict__ Ut, const E* __restrict__ Lm,
+                                         const E* __restrict__ pI1, const E* __restrict__ pJ1, int ti, int tj, int si,
+                                         int sj, bool hc, bool hr, int g, int c, E w0, E w1, E& m0, E& m1) {
+  const int R = 8 * ti, C = 8 * tj;
+  if (hc) blk_col_product(Xv + 8 * si * kXP + C, Ut + (8 * si - 1) * kUP + R, pI1 + 8 * si - 1, g, c, w0, w1, m0, m1);
+  if (hr) blk_row_product(Xv + R * kXP + 8 * sj, Lm + 8 * sj * kLP + C, pJ1 + 8 * sj, g, c, w0, w1, m0, m1);
 }
 
 // The whole in-tile solve (all 8 compute warps; ends with Xv final).
 template <typename E>
-__device__ __forceinline__ void tile_solve_blocks(const BlkView<E>& v, int warp, int lane) {
+__device__ __forceinline__ void tile_solve_blocks(E* __restrict__ Xv, E* __restrict__ acc, const E* __restrict__ Ut,
+                                                  const E* __restrict__ Lm, const E* __restrict__ pI,
+                                                  const E* __restrict__ pI1, const E* __restrict__ pJ1, int warp,
+                                                  int lane) {
   const int g = lane >> 3, c = lane & 7;
 #pragma unroll 1
   for (int s = 0; s < 7; ++s) {
@@ -189,34 +196,36 @@ __device__ __forceinline__ void tile_solve_blocks(const BlkView<E>& v, int warp,
     if (warp < nb) {
       const int bi = bi0 + warp, bj = bi + E_;
       const int R = 8 * bi, C = 8 * bj;
-      const E pj = v.pJ1[C + c];
-      const E w0 = v.pI[R + g] * pj, w1 = v.pI[R + g + 4] * pj;
-      E v0 = v.acc[(R + g) * v.XP + C + c];
-      E v1 = v.acc[(R + g + 4) * v.XP + C + c];
-      if (bi < 3) blk_col_product(v, R, C, bi + 1, g, c, w0, w1, v0, v1);  // block below, finished last step
-      if (bj > 0) blk_row_product(v, R, C, bj - 1, g, c, w0, w1, v0, v1);  // block to the left
-      blk_solve8(v, R, C, g, c, w0, w1, v0, v1);
+      const E pj = pJ1[C + c];
+      const E w0 = pI[R + g] * pj, w1 = pI[R + g + 4] * pj;
+      E v0 = acc[(R + g) * kXP + C + c];
+      E v1 = acc[(R + g + 4) * kXP + C + c];
+      // splits from the two neighbour blocks finished in the previous step
+      blk_fold(Xv, Ut, Lm, pI1, pJ1, bi, bj, bi + 1, bj - 1, bi < 3, bj > 0, g, c, w0, w1, v0, v1);
+      blk_solve8(Xv + R * kXP + C, Ut + (R - 1) * kUP + R, Lm + C * kLP + C, pI1 + R - 1, pJ1 + C, g, c, w0, w1, v0,
+                 v1);
     } else if (s >= 1) {
       // fold the blocks of diagonal E_-1 into the blocks on diagonals >= E_+1
       const int idle = warp - nb, nidle = 8 - nb;
       const int Es = E_ - 1;
-      int k = 0;
+      int k = 0, next = idle;
+#pragma unroll 1
       for (int blk = 0; blk < 16; ++blk) {
         const int ti = blk >> 2, tj = blk & 3;
         if (tj - ti < E_ + 1) continue;
         const int si = tj - Es, sj = ti + Es;
         const bool hc = si > ti && si <= 3, hr = sj >= 0 && sj < tj;
         if (!hc && !hr) continue;
-        if ((k++ % nidle) != idle) continue;
+        if (k++ != next) continue;
+        next += nidle;
         const int R = 8 * ti, C = 8 * tj;
-        const E pj = v.pJ1[C + c];
-        const E w0 = v.pI[R + g] * pj, w1 = v.pI[R + g + 4] * pj;
-        E m0 = v.acc[(R + g) * v.XP + C + c];
-        E m1 = v.acc[(R + g + 4) * v.XP + C + c];
-        if (hc) blk_col_product(v, R, C, si, g, c, w0, w1, m0, m1);
-        if (hr) blk_row_product(v, R, C, sj, g, c, w0, w1, m0, m1);
-        v.acc[(R + g) * v.XP + C + c] = m0;
-        v.acc[(R + g + 4) * v.XP + C + c] = m1;
+        const E pj = pJ1[C + c];
+        const E w0 = pI[R + g] * pj, w1 = pI[R + g + 4] * pj;
+        E m0 = acc[(R + g) * kXP + C + c];
+        E m1 = acc[(R + g + 4) * kXP + C + c];
+        blk_fold(Xv, Ut, Lm, pI1, pJ1, ti, tj, si, sj, hc, hr, g, c, w0, w1, m0, m1);
+        acc[(R + g) * kXP + C + c] = m0;
+        acc[(R + g + 4) * kXP + C + c] = m1;
       }
     }
     bar_compute();
@@ -552,8 +561,7 @@ __global__ void __launch_bounds__(kMcmThreads, 3) mcm_main_kernel(const McmLaunc
             }
             bar_compute();
             {
-              const BlkView<E> bv{Xv, accv, Ut, Lm, pv, pv + T, pv + 2 * T, SM::UP, SM::LP, SM::XP};
-              tile_solve_blocks<E>(bv, warp, lane);
+              tile_solve_blocks<E>(Xv, accv, Ut, Lm, pv, pv + T, pv + 2 * T, warp, lane);
             }
             // ---------------- outputs needed by other tiles, then publish ----------------
             const int64_t nn = n;
@@ -611,23 +619,15 @@ __global__ void __launch_bounds__(kMcmThreads, 3) mcm_main_kernel(const McmLaunc
               __threadfence();
               st_release(a.flags + tidx, 1);
             }
-            // ---------------- split table: smallest k reaching the final value ----------------
-            // k order: column splits IT+li..IT+30 < boundary IT+31 < external splits < row splits JT+u
-            const unsigned long long kmask = (1ull << KB) - 1ull;
-#pragma unroll 1
+            // provisional split: k of the external minimum (-1 if none); the split
+            // pass replaces it by the smallest k over all splits reaching the value
+#pragma unroll
             for (int r = 0; r < 4; ++r) {
               const int li = 4 * w + r;
-              const E v = vals[r];
-              const E w0 = pi[r] * pj1;
-              int k = -1;
-              for (int t = li; t <= T - 2 && k < 0; ++t)
-                if (Ut[t * SM::UP + li] + Xv[(t + 1) * SM::XP + lane] + w0 * pv[T + t] == v) k = IT + t;
-              if (k < 0 && bnd[r] == v) k = IT + T - 1;
-              if (k < 0 && (E)(bestS[li * T + lane] >> KB) == v) k = (int)(bestS[li * T + lane] & kmask);
-              for (int u = 0; u < lane && k < 0; ++u)
-                if (Xv[li * SM::XP + u] + Lm[u * SM::LP + lane] + w0 * pv[2 * T + u] == v) k = JT + u;
               const int64_t i = IT + li, j = JT + lane;
-              if (i < nn && j < nn) inst.s[i * nn + j] = (int16_t)k;
+              const unsigned long long ek = bestS[li * T + lane];
+              const int kx = (ek >> KB) == (~0ull >> KB) ? -1 : (int)(ek & ((1ull << KB) - 1ull));
+              if (i < nn && j < nn) inst.s[i * nn + j] = (int16_t)kx;
             }
           } else {
             // diagonal tile: ordinary MCM on the 32-matrix sub-chain
@@ -725,8 +725,8 @@ __global__ void __launch_bounds__(kMcmThreads, 3) mcm_main_kernel(const McmLaunc
       __threadfence();
       if (!finisher)
         red_release_add(a.counters + tidx, 1);
-      else if (D == 0)
-        st_release(a.flags + tidx, 1);  // off-diagonal tiles publish right after their values
+      else if (D == 0)  // off-diagonal tiles publish right after their values
+        st_release(a.flags + tidx, 1);
     }
   }
 }
@@ -798,6 +798,70 @@ __global__ void __launch_bounds__(256) mcm_prologue_kernel(const McmLaunchArgs a
   }
 }
 
+// Split pass for off-diagonal tiles: replaces the provisional split (k of
+// the smallest external candidate) by the smallest k over ALL splits whose
+// candidate equals the final m[i][j], scanning in increasing k: column splits
+// k = IT+li .. IT+30, the boundary split IT+31, the external split, the row
+// splits JT .. j-1.  Reads only the final table and the dims.
+template <bool I64>
+__global__ void __launch_bounds__(256) mcm_splits_kernel(const McmLaunchArgs a) {
+  using E = typename Cost<I64>::E;
+  __shared__ E Us[T][T + 1];   // Us[li][t]  = m[IT+li][IT+t]
+  __shared__ E Xs[T + 1][T + 1];  // Xs[r][lj] = m[IT+r][JT+lj], r = 0..32 (row 32: boundary row)
+  __shared__ E Ls[T][T + 1];   // Ls[u][lj] = m[JT+u+1][JT+lj]
+  __shared__ E pI[T + 1], pJ[T + 1];  // p[IT + x], p[JT + x + 1]
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  // after a device-reported error the tables (and provisional splits) were
+  // never written: touch nothing
+  if (*reinterpret_cast<volatile int32_t*>(a.status) != 0) return;
+  for (int t = blockIdx.x; t < a.ntasks; t += gridDim.x) {
+    const McmTask task = a.tasks[t];
+    const int I = task.I, J = task.J;
+    if (task.kind != 0 || J == I) continue;  // diagonal tiles compute exact splits themselves
+    const McmInstDev in = a.insts[task.inst];
+    const int64_t n = in.n;
+    const int IT = I * T, JT = J * T;
+    const E* m = static_cast<const E*>(in.m);
+    __syncthreads();
+    for (int idx = tid; idx < T * T; idx += blockDim.x) {
+      const int r = idx >> 5, x = idx & 31;
+      const int64_t gi = IT + r;
+      Us[r][x] = (gi < n && IT + x < n) ? m[gi * n + IT + x] : (E)0;
+      Xs[r][x] = (gi < n && JT + x < n) ? m[gi * n + JT + x] : (E)0;
+      const int64_t gl = JT + r + 1;
+      Ls[r][x] = (gl < n && JT + x < n) ? m[gl * n + JT + x] : (E)0;
+    }
+    if (tid < T) {
+      const int64_t gb = IT + T;
+      Xs[T][tid] = (gb < n && JT + tid < n) ? m[gb * n + JT + tid] : (E)0;
+    }
+    if (tid <= T) {
+      pI[tid] = (IT + tid <= n) ? (E)in.p[IT + tid] : (E)1;
+      pJ[tid] = (JT + tid + 1 <= n) ? (E)in.p[JT + tid + 1] : (E)1;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+      const int li = 4 * w + r;
+      const int64_t i = IT + li, j = JT + lane;
+      if (i >= n || j >= n) continue;
+      const E v = Xs[li][lane];
+      const E pij = pI[li] * pJ[lane];  // p[i] * p[j+1]
+      int k = -1;
+      for (int tt = li; tt <= T - 1 && k < 0; ++tt)  // column splits and (tt = 31) the boundary split
+        if (Us[li][tt] + Xs[tt + 1][lane] + pij * pI[tt + 1] == v) k = IT + tt;
+      if (k < 0) {
+        const int kx = in.s[i * n + j];  // external splits lie in [IT + 32, JT - 1]
+        if (kx >= IT + T && kx < JT && m[i * n + kx] + m[(int64_t)(kx + 1) * n + j] + pij * (E)in.p[kx + 1] == v)
+          k = kx;
+      }
+      for (int u = 0; u < lane && k < 0; ++u)
+        if (Xs[li][u] + Ls[u][lane] + pij * pJ[u] == v) k = JT + u;
+      in.s[i * n + j] = (int16_t)k;
+    }
+  }
+}
+
 }  // namespace
 
 size_t mcm_smem_bytes(bool i64) { return i64 ? Smem<true>::TOTAL : Smem<false>::TOTAL; }
@@ -824,6 +888,15 @@ cudaError_t launch_mcm_prologue(const McmLaunchArgs& a, bool i64, cudaStream_t s
     mcm_prologue_kernel<true><<<a.ninst, 256, 0, st>>>(a);
   else
     mcm_prologue_kernel<false><<<a.ninst, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mcm_splits(const McmLaunchArgs& a, bool i64, int grid, cudaStream_t st) {
+  if (a.ntasks <= 0) return cudaSuccess;
+  if (i64)
+    mcm_splits_kernel<true><<<grid, 256, 0, st>>>(a);
+  else
+    mcm_splits_kernel<false><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -175,6 +175,7 @@ dp_status launch_mcm_group(Server* S, const std::vector<Req*>& reqs, bool i64, L
   sp->d_tasks = reinterpret_cast<dpk::McmTask*>(ws + o_tasks);
   sp->d_accslot = reinterpret_cast<int32_t*>(ws + o_acc);
   sp->d_insts = reinterpret_cast<dpk::McmInstDev*>(ws + o_insts);
+
   if ((e = cudaMemcpyAsync(ws, hp, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return fail_cuda(e, "serve: upload");
   if ((e = cudaMemsetAsync(d_status, 0, 4, st)) != cudaSuccess) return fail_cuda(e, "serve: status");
