@@ -99,6 +99,32 @@ dp_status dp_profile_end(double *mcm_ms, int64_t *mcm_launches, double *sdp_ms, 
 dp_status mcm_solve(const int32_t *p, int32_t n, dp_cost ct, void *m, int16_t *s,
                     int32_t *status_dev, void *stream);
 
+/* mcm_solve for int32 costs that allocates no memory.  The paper has no
+ * counterpart: it exists for callers that cannot allocate when they solve --
+ * a process whose free device memory belongs to its own allocator (where a
+ * stream-ordered allocation would fail or grow the pool), or a
+ * latency-critical loop that must not enter an allocator.
+ *   p, n, m, s  as for mcm_solve with ct = DP_COST_I32; m is int32[n*n].
+ *   n           1 <= n <= 1024: the scratch is a fixed file-scope device
+ *               array of 8,708,864 bytes per device; a larger n returns
+ *               DP_EINVAL without touching the device.
+ *   status_dev  required (NULL is DP_EINVAL): caller-owned device int32 that
+ *               is zero on entry; device-side errors land there, read them
+ *               with dp_sync_status(stream, status_dev).
+ * The first call on a device does the set-up for that device (loads the
+ * module that holds the scratch, takes the scratch's address on that device
+ * with cudaGetSymbolAddress, sets kernel attributes); make it before any
+ * stream capture.  Every call then starts with a set-up kernel that writes
+ * all of the scratch a solve reads before writing it: the tile flags, bulk
+ * counters and queue counter, which must start at zero, the accumulators
+ * (all ones) and the work queue.  So the scratch needs no initial contents
+ * and a failed call leaves nothing that the next one depends on.
+ * One device has one scratch: calls that overlap in time on the same device
+ * (two streams, or two host threads whose calls are not ordered on one
+ * stream) race on it and corrupt each other's results. */
+dp_status mcm_solve_noalloc(const int32_t *p, int32_t n, int32_t *m, int16_t *s, int32_t *status_dev,
+                            void *stream);
+
 /* Same computation with HOST buffers: copies p (n+1 int32) to the device,
  * solves, copies m and s back, and waits for completion.  Host buffers may be
  * pageable or pinned (pinned is faster). */

@@ -89,6 +89,21 @@ def mcm_solve(p, cost="i32", m=None, s=None, status=None, stream=None):
     return m, s
 
 
+def mcm_solve_noalloc(p, m, s, status, stream=None):
+    """mcm_solve for int32 costs through the entry point that allocates
+    nothing: the caller passes every buffer (p int32 n+1, m int32 and s int16
+    of n*n, status int32 holding 0), n <= 1024."""
+    torch = _torch()
+    lib = native.load()
+    _need(p, torch.int32, "p")
+    n = p.numel() - 1
+    _need(m, torch.int32, "m", n * n)
+    _need(s, torch.int16, "s", n * n)
+    _need(status, torch.int32, "status", 1)
+    check(lib.mcm_solve_noalloc(_ptr(p), n, _ptr(m), _ptr(s), _ptr(status), _stream_ptr(stream)))
+    return m, s
+
+
 def mcm_solve_host(p, cost="i32", m=None, s=None, stream=None):
     """Host-buffer form: numpy (or pinned torch CPU) dims in, tables out."""
     lib = native.load()

@@ -130,10 +130,8 @@ McmStatic::~McmStatic() {
 }
 
 namespace {
-// Levels of ready-diagonal grouped into one bulk task, and the smallest number
-// of bulk levels for which a tile is split at all.
-constexpr int kLevelsPerPart = 4;
-constexpr int kMinBulkLevels = 2;
+using dpk::kLevelsPerPart;
+using dpk::kMinBulkLevels;
 
 // Queue order: by the tile-diagonal at which a task becomes ready; within a
 // diagonal, finishers (the critical path) before bulk tasks.

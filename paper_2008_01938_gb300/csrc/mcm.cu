@@ -882,6 +882,19 @@ cudaError_t mcm_occupancy(bool i64, int* blocks_per_sm) {
                                                        Smem<false>::TOTAL);
 }
 
+cudaError_t mcm_preload(bool i64) {
+  cudaFuncAttributes fa;
+  cudaError_t e;
+  if (i64) {
+    if ((e = cudaFuncGetAttributes(&fa, mcm_prologue_kernel<true>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, mcm_main_kernel<true>)) != cudaSuccess) return e;
+    return cudaFuncGetAttributes(&fa, mcm_splits_kernel<true>);
+  }
+  if ((e = cudaFuncGetAttributes(&fa, mcm_prologue_kernel<false>)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&fa, mcm_main_kernel<false>)) != cudaSuccess) return e;
+  return cudaFuncGetAttributes(&fa, mcm_splits_kernel<false>);
+}
+
 cudaError_t launch_mcm_prologue(const McmLaunchArgs& a, bool i64, cudaStream_t st) {
   if (a.ninst <= 0) return cudaSuccess;
   if (i64)

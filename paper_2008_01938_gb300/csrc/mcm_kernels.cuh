@@ -52,6 +52,13 @@ constexpr int kComputeThreads = 2 * kGroupThreads;     // two groups
 constexpr int kMcmThreads = kComputeThreads + 32;      // + producer warp
 constexpr int kStages = 2;                             // bulk-copy stages per group
 
+// Work split of a tile on tile-diagonal D >= 2: its external levels
+// r = (D+1)/2 .. D-1 go to bulk tasks of kLevelsPerPart levels each, except
+// the last level, which the finisher keeps; a tile with fewer than
+// kMinBulkLevels bulk levels is not split at all.
+constexpr int kLevelsPerPart = 4;
+constexpr int kMinBulkLevels = 2;
+
 struct McmInstDev {
   const int32_t* p;   // dims p[0..n] (set by the prologue)
   void* m;            // output cost table (set by the prologue)
@@ -105,5 +112,8 @@ cudaError_t mcm_occupancy(bool i64, int* blocks_per_sm);
 cudaError_t launch_mcm_prologue(const McmLaunchArgs& a, bool i64, cudaStream_t st);
 cudaError_t launch_mcm_main(const McmLaunchArgs& a, bool i64, int grid, cudaStream_t st);
 cudaError_t launch_mcm_splits(const McmLaunchArgs& a, bool i64, int grid, cudaStream_t st);
+// Loads the prologue, main and split-pass kernels into the current context
+// (with lazy module loading a kernel is otherwise loaded at its first launch).
+cudaError_t mcm_preload(bool i64);
 
 }  // namespace dpk
