@@ -230,6 +230,20 @@ class SdpPlan:
 # Serving
 # ---------------------------------------------------------------------------
 
+class _CudaArray:
+    """__cuda_array_interface__ over a raw device pointer (for torch.as_tensor)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+def _device_view(ptr, shape, typestr):
+    torch = _torch()
+    if not ptr:
+        raise ValueError("result holds no device table")
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
+
 class Server:
     """Continuous-batching request server (serve_create / serve_submit /
     serve_poll / serve_release / serve_destroy)."""
@@ -276,6 +290,17 @@ class Server:
 
     def release(self, ticket):
         check(native.load().serve_release(self._h, ticket))
+
+    @staticmethod
+    def tables(res, cost="i64"):
+        """Zero-copy torch views of a finished request's server-owned device
+        tables, valid until release: (m, s) for MCM (``cost`` as submitted),
+        ST (int32 holding uint32) for S-DP."""
+        n = int(res.n)
+        if res.kind == native.DP_REQ_MCM:
+            dt = "<i8" if _cost(cost) == native.DP_COST_I64 else "<i4"
+            return _device_view(res.m_dev, (n, n), dt), _device_view(res.s_dev, (n, n), "<i2")
+        return _device_view(res.st_dev, (n,), "<i4")
 
     def close(self):
         if getattr(self, "_h", None):

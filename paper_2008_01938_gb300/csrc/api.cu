@@ -306,8 +306,6 @@ dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const i
   if ((e = dpk::launch_mcm_main(a, sp.i64, std::max(grid, 1), st)) != cudaSuccess)
     return fail_cuda(e, "launch MCM kernel");
   if (prof) profile_mark(0, st, true);
-  if ((e = dpk::launch_mcm_splits(a, sp.i64, ds->sms * 8, st)) != cudaSuccess)
-    return fail_cuda(e, "launch MCM split pass");
   return DP_OK;
 }
 

@@ -12,9 +12,7 @@ namespace dpk {
 namespace {
 
 constexpr int T = kTile;
-constexpr int kUP = 36;  // pitch of U^T in shared memory (bank-conflict free for the block solve)
-constexpr int kLP = 40;  // pitch of L
-constexpr int kXP = 33;  // pitch of X and of the running minima
+constexpr int kDiagRows = 2 * T;  // cell diagonals e = lj - li in [-31, 31] (dI = e + 31), one spare row
 
 template <bool I64>
 struct Cost {
@@ -26,18 +24,37 @@ __device__ __forceinline__ int64_t tile_index(const McmInstDev& in, int I, int J
   return in.tile_base + (int64_t)I * in.nt - (int64_t)I * (I - 1) / 2 + (J - I);
 }
 
-// Shared-memory carve-up (byte offsets); identical for all blocks.  During a
-// finisher's in-tile solve the bulk-copy stages are idle (every copy of the
-// task has landed), so the solve's working arrays are carved from them.
+// Shared-memory carve-up (byte offsets); identical for all blocks.
+//
+// In-tile wavefront arrays (finisher of an off-diagonal tile) start at STA and
+// reuse the bulk-copy stages (every copy of the task has landed before they
+// are written); where they need more room than the stages, the finisher
+// buffers that follow are moved up.  Row indices of the U^T / L tables:
+//   int32: row = t + 32 for t in [-32, 63] (96 rows, constant offsets per step)
+//   int64: row = t & 63 (64 rows; saves the shared memory that keeps two
+//          int64 blocks resident per SM)
+// Rows outside t = 0 .. 30 hold zeros.
 template <bool I64>
 struct Smem {
   static constexpr int ES = I64 ? 8 : 4;
   static constexpr int TILE = T * T * ES;
+  static constexpr bool kPadRows = !I64;
+  static constexpr int kRows = kPadRows ? 96 : 64;
+  static constexpr int kRowOff = kPadRows ? 32 : 0;
+  static constexpr int UPW = I64 ? 34 : 36;                       // U^T pitch: 16-byte rows, conflict-free
   static constexpr int BARS = 0;                                 // 9 mbarriers + task slot
   static constexpr int STA = 128;                                // [group][stage] row panels
   static constexpr int STB = STA + 4 * TILE;                     // [group][stage] column panels
   static constexpr int STPK = STB + 4 * TILE;                    // [group][stage] 32 x u32 dims
-  static constexpr int FINU = STPK + 4 * 128;                    // row panel of diagonal tile (I,I)
+  static constexpr int STEND = STPK + 4 * 128;
+  static constexpr int WUP = STA;                                // Up[row(t)][li] = m[IT+li][IT+t]
+  static constexpr int WLP = WUP + ((kRows * UPW * ES + 127) / 128) * 128;  // Lp[row(u)][lj] = m[JT+u+1][JT+lj]
+  static constexpr int WXR = WLP + kRows * T * ES;               // Xr[e+31][li]: final value of cell (li, li+e)
+  static constexpr int WXC = WXR + kDiagRows * T * ES;           // Xc[e+31][lj]: final value of cell (lj-e, lj)
+  static constexpr int WPKI = WXC + kDiagRows * T * ES;          // PKIp[row(t)] = p[IT+t+1]
+  static constexpr int WPKJ = WPKI + kRows * 4;                  // PKJp[row(u)] = p[JT+u+1]
+  static constexpr int WEND = WPKJ + kRows * 4;
+  static constexpr int FINU = ((STEND > WEND ? STEND : WEND) + 127) / 128 * 128;  // row panel of (I,I)
   static constexpr int FINL = FINU + TILE;                       // column panel of diagonal tile (J,J)
   static constexpr int FINBROW = FINL + TILE;                    // boundary row (one tile row)
   static constexpr int FINPP = FINBROW + 256;                    // p[32I .. 32I+31]
@@ -46,15 +63,9 @@ struct Smem {
   static constexpr int FINACC = FINPKJ + 128;                    // bulk-task partial minima
   static constexpr int BEST = FINACC + T * T * 8;                // running (value, k) keys
   static constexpr int TOTAL = BEST + T * T * 8;
-  // in-tile solve arrays, inside the stage area (pitch 32 everywhere: the
-  // access patterns of the pipelined solve are bank-conflict free with it)
-  static constexpr int UP = kUP, LP = kLP, XP = kXP;
-  static constexpr int UT = STA;                                 // U^T[t][li] = m[IT+li][IT+t]
-  static constexpr int LM = UT + ((T * UP * ES + 127) / 128) * 128;  // L[u][lj] = m[JT+u+1][JT+lj]
-  static constexpr int XV = LM + ((T * LP * ES + 127) / 128) * 128;  // final values of the tile
-  static constexpr int ACCV = XV + ((T * XP * ES + 127) / 128) * 128;  // running minima of older splits
-  static constexpr int PV = ACCV + ((T * XP * ES + 127) / 128) * 128;  // p[IT+li], p[IT+t+1], p[JT+u+1]
-  static_assert(PV + 3 * T * ES <= STPK, "in-tile arrays must fit in the stage area");
+  static constexpr int XV = STA;                                 // diagonal tiles: the tile's values
+  __host__ __device__ static constexpr int row(int t) { return kPadRows ? t + kRowOff : (t & 63); }
+  static_assert(WXR % 16 == 0 && WUP % 16 == 0 && (UPW * ES) % 16 == 0, "16-byte vector rows");
 };
 
 __device__ __forceinline__ void bar_compute() {  // the 256 compute threads only
@@ -86,150 +97,89 @@ __device__ __forceinline__ E umin(E a, E b) { return a < b ? a : b; }
 //   column splits k = IT + t, li <= t <= 30:  U[li][t] + X[t+1][lj] + w
 //   row splits    k = JT + u,  0 <= u < lj:   X[li][u] + L[u][lj] + w
 // with U = the diagonal tile (I, I), L = rows shifted by one of (J, J) and
-// w = p[IT+li] p[k+1] p[JT+lj+1].
-// The tile is cut into 4 x 4 blocks of 8 x 8; block (bi, bj) depends on the
-// blocks below it in its column and left of it in its row.  Blocks are solved
-// one block-diagonal E = bj - bi at a time (7 steps), one warp per block:
-//   * the warp first folds in the splits whose operand lies in the two
-//     neighbour blocks finished in the previous step (8x8x8 products);
-//   * then it runs the paper's diagonal-order wavefront over the block's 15
-//     cell diagonals with warp shuffles only (lane = column c + 8 g, cells of
-//     rows g and g + 4);
-//   * warps without a block in this step fold the previous step's blocks into
-//     the blocks two or more diagonals ahead.
-// Only values are carried; the split index is recovered after the tile is
-// published.
+// w = p[IT+li] p[k+1] p[JT+lj+1]; the boundary split k = IT + 31 and the
+// external splits are known before the solve starts.
+//
+// Cell (li, lj) lies on cell diagonal e = lj - li in [-31, 31] and depends
+// only on cells of lower diagonals, so the tile is solved in the paper's
+// diagonal order (Figs. 4-6), one diagonal per step: in step e every cell
+// pulls the candidate of its row split and of its column split whose operand
+// lies on diagonal e (exactly one of each), and the cells of diagonal e + 1,
+// whose last operands were on diagonal e, become final.  Warp w owns rows
+// 4w .. 4w+3 and lane = column.
+//
+// Each thread keeps one running minimum per cell (values only).  The operands
+// that do not depend on the tile move predictably from step to step and are
+// loaded ahead of the barrier: the row split of cell (li, lj) at step e uses
+// L[li + e][lj], the thread's 4 rows use 4 consecutive rows of L, so a
+// 4-entry register window gains one new row per step; U[li][lj - e - 1] and
+// p[IT + lj - e] come from one 16-byte load and one word per step.  The cell
+// values themselves are exchanged through two diagonal-major arrays written
+// once, when a cell becomes final: Xr (indexed by row, the row-split operand)
+// and Xc (indexed by column, the column-split operand).
+//
+// Out-of-range operands are read from zero rows (U, L, dims) and from
+// all-ones entries (cells that do not exist), so no candidate needs a
+// predicate: a missing cell yields an all-ones candidate, and a candidate
+// whose operand exists but whose split is outside the cell's range only
+// arises after the cell was finalised (its running minimum is then dead).
+// The smallest minimising split is recovered after the tile is published, by
+// scanning the splits of each cell in increasing k.
 // ---------------------------------------------------------------------------
-
-// Column splits of the lane's two cells (rows R + g, R + g + 4, column C + c)
-// whose second operand lies in block row si (rows 8si .. 8si+7).  Pointers
-// are rebased so that the loop indexes with lane constants only:
-//   xs = Xv + (8si)*XP + C, us = Ut + (8si-1)*UP + R, ps = pI1 + 8si - 1.
 template <typename E>
-__device__ __forceinline__ void blk_col_product(const E* __restrict__ xs, const E* __restrict__ us,
-                                                const E* __restrict__ ps, int g, int c, E w0, E w1, E& m0, E& m1) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const E x = xs[q * kXP + c];
-    const E pk = ps[q];
-    m0 = umin(m0, us[q * kUP + g] + x + w0 * pk);
-    m1 = umin(m1, us[q * kUP + g + 4] + x + w1 * pk);
+struct Vec4 {
+  E v[4];
+};
+
+template <typename E>
+__device__ __forceinline__ Vec4<E> lds4(const E* p) {  // 4 consecutive elements, 16-byte aligned
+  Vec4<E> r;
+  if constexpr (sizeof(E) == 4) {
+    const uint4 q = *reinterpret_cast<const uint4*>(p);
+    r.v[0] = q.x, r.v[1] = q.y, r.v[2] = q.z, r.v[3] = q.w;
+  } else {
+    const ulonglong2 q0 = *reinterpret_cast<const ulonglong2*>(p);
+    const ulonglong2 q1 = *reinterpret_cast<const ulonglong2*>(p + 2);
+    r.v[0] = q0.x, r.v[1] = q0.y, r.v[2] = q1.x, r.v[3] = q1.y;
+  }
+  return r;
+}
+
+// a[r] for a runtime r in 0..3 as a chain of predicated selects (a C
+// conditional chain here is compiled to divergent branches, which cost
+// several times more inside the wavefront step).
+template <typename E>
+__device__ __forceinline__ E sel4(int r, E a0, E a1, E a2, E a3) {
+  if constexpr (sizeof(E) == 4) {
+    uint32_t v;
+    asm("{\n\t.reg .pred p1, p2, p3;\n\t"
+        "setp.eq.s32 p1, %5, 1;\n\tsetp.eq.s32 p2, %5, 2;\n\tsetp.eq.s32 p3, %5, 3;\n\t"
+        "selp.b32 %0, %2, %1, p1;\n\tselp.b32 %0, %3, %0, p2;\n\tselp.b32 %0, %4, %0, p3;\n\t}"
+        : "=r"(v)
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(r));
+    return v;
+  } else {
+    unsigned long long v;
+    asm("{\n\t.reg .pred p1, p2, p3;\n\t"
+        "setp.eq.s32 p1, %5, 1;\n\tsetp.eq.s32 p2, %5, 2;\n\tsetp.eq.s32 p3, %5, 3;\n\t"
+        "selp.b64 %0, %2, %1, p1;\n\tselp.b64 %0, %3, %0, p2;\n\tselp.b64 %0, %4, %0, p3;\n\t}"
+        : "=l"(v)
+        : "l"(a0), "l"(a1), "l"(a2), "l"(a3), "r"(r));
+    return v;
   }
 }
 
-// Row splits of the lane's two cells whose first operand lies in block
-// column sj (columns 8sj .. 8sj+7):
-//   xr = Xv + R*XP + 8sj, ls = Lm + (8sj)*LP + C, ps = pJ1 + 8sj.
+// Shared-memory store of v at 32-bit shared address addr when p holds.
 template <typename E>
-__device__ __forceinline__ void blk_row_product(const E* __restrict__ xr, const E* __restrict__ ls,
-                                                const E* __restrict__ ps, int g, int c, E w0, E w1, E& m0, E& m1) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const E l = ls[q * kLP + c];
-    const E pk = ps[q];
-    m0 = umin(m0, xr[g * kXP + q] + l + w0 * pk);
-    m1 = umin(m1, xr[(g + 4) * kXP + q] + l + w1 * pk);
-  }
-}
-
-// Wavefront over one 8x8 block (origin R0, C0) by one warp; v0 / v1 hold the
-// minima of all splits outside the block for the lane's two cells on entry
-// and the final values on exit (also stored to X).  Rebased pointers:
-//   xb = Xv + R0*XP + C0, ub = Ut + (R0-1)*UP + R0 (so ub[a*UP + r] = U[R0+r][R0+a-1]),
-//   lb = Lm + C0*LP + C0, pi1 = pI1 + R0 - 1, pj1 = pJ1 + C0.
-template <typename E>
-__device__ __forceinline__ void blk_solve8(E* __restrict__ xb, const E* __restrict__ ub, const E* __restrict__ lb,
-                                           const E* __restrict__ pi1, const E* __restrict__ pj1, int g, int c, E w0,
-                                           E w1, E& v0, E& v1) {
-  const int r0 = g, r1 = g + 4;
-#pragma unroll
-  for (int e = -7; e <= 7; ++e) {
-    const E xe = (c - r0 == e) ? v0 : v1;  // this lane's cell on diagonal e, if any
-    const int a = c - e;                   // column split from row a of the block
-    const int ac = a < 1 ? 1 : (a > 7 ? 7 : a);
-    const E xa = __shfl_sync(0xffffffffu, xe, (ac & 3) * 8 + c);
-    const int b0 = r0 + e, b1 = r1 + e;    // row splits from columns b0, b1
-    const int b0c = b0 < 0 ? 0 : (b0 > 7 ? 7 : b0), b1c = b1 < 0 ? 0 : (b1 > 7 ? 7 : b1);
-    const E xb0 = __shfl_sync(0xffffffffu, xe, g * 8 + b0c);
-    const E xb1 = __shfl_sync(0xffffffffu, xe, g * 8 + b1c);
-    const E pkt = pi1[ac];
-    const E ca0 = ub[ac * kUP + r0] + xa + w0 * pkt;
-    const E ca1 = ub[ac * kUP + r1] + xa + w1 * pkt;
-    const E cb0 = xb0 + lb[b0c * kLP + c] + w0 * pj1[b0c];
-    const E cb1 = xb1 + lb[b1c * kLP + c] + w1 * pj1[b1c];
-    if (c - r0 > e) {
-      if (a <= 7) v0 = umin(v0, ca0);
-      if (b0 >= 0) v0 = umin(v0, cb0);
-    }
-    if (c - r1 > e) {
-      if (a <= 7) v1 = umin(v1, ca1);
-      if (b1 >= 0) v1 = umin(v1, cb1);
-    }
-  }
-  xb[r0 * kXP + c] = v0;
-  xb[r1 * kXP + c] = v1;
-}
-
-// Folds into block (ti, tj) the splits whose operand lies in block (si, tj)
-// below it (hc) and / or block (ti, sj) left of it (hr); m0 / m1 in/out.
-template <typename E>
-__device__ __forceinline__ void blk_fold(const E* __restrict__ Xv, const E* __restrict__ Ut, const E* __restrict__ Lm,
-                                         const E* __restrict__ pI1, const E* __restrict__ pJ1, int ti, int tj, int si,
-                                         int sj, bool hc, bool hr, int g, int c, E w0, E w1, E& m0, E& m1) {
-  const int R = 8 * ti, C = 8 * tj;
-  if (hc) blk_col_product(Xv + 8 * si * kXP + C, Ut + (8 * si - 1) * kUP + R, pI1 + 8 * si - 1, g, c, w0, w1, m0, m1);
-  if (hr) blk_row_product(Xv + R * kXP + 8 * sj, Lm + 8 * sj * kLP + C, pJ1 + 8 * sj, g, c, w0, w1, m0, m1);
-}
-
-// The whole in-tile solve (all 8 compute warps; ends with Xv final).
-template <typename E>
-__device__ __forceinline__ void tile_solve_blocks(E* __restrict__ Xv, E* __restrict__ acc, const E* __restrict__ Ut,
-                                                  const E* __restrict__ Lm, const E* __restrict__ pI,
-                                                  const E* __restrict__ pI1, const E* __restrict__ pJ1, int warp,
-                                                  int lane) {
-  const int g = lane >> 3, c = lane & 7;
-#pragma unroll 1
-  for (int s = 0; s < 7; ++s) {
-    const int E_ = s - 3;
-    const int nb = 4 - (E_ < 0 ? -E_ : E_);
-    const int bi0 = E_ < 0 ? -E_ : 0;
-    if (warp < nb) {
-      const int bi = bi0 + warp, bj = bi + E_;
-      const int R = 8 * bi, C = 8 * bj;
-      const E pj = pJ1[C + c];
-      const E w0 = pI[R + g] * pj, w1 = pI[R + g + 4] * pj;
-      E v0 = acc[(R + g) * kXP + C + c];
-      E v1 = acc[(R + g + 4) * kXP + C + c];
-      // splits from the two neighbour blocks finished in the previous step
-      blk_fold(Xv, Ut, Lm, pI1, pJ1, bi, bj, bi + 1, bj - 1, bi < 3, bj > 0, g, c, w0, w1, v0, v1);
-      blk_solve8(Xv + R * kXP + C, Ut + (R - 1) * kUP + R, Lm + C * kLP + C, pI1 + R - 1, pJ1 + C, g, c, w0, w1, v0,
-                 v1);
-    } else if (s >= 1) {
-      // fold the blocks of diagonal E_-1 into the blocks on diagonals >= E_+1
-      const int idle = warp - nb, nidle = 8 - nb;
-      const int Es = E_ - 1;
-      int k = 0, next = idle;
-#pragma unroll 1
-      for (int blk = 0; blk < 16; ++blk) {
-        const int ti = blk >> 2, tj = blk & 3;
-        if (tj - ti < E_ + 1) continue;
-        const int si = tj - Es, sj = ti + Es;
-        const bool hc = si > ti && si <= 3, hr = sj >= 0 && sj < tj;
-        if (!hc && !hr) continue;
-        if (k++ != next) continue;
-        next += nidle;
-        const int R = 8 * ti, C = 8 * tj;
-        const E pj = pJ1[C + c];
-        const E w0 = pI[R + g] * pj, w1 = pI[R + g + 4] * pj;
-        E m0 = acc[(R + g) * kXP + C + c];
-        E m1 = acc[(R + g + 4) * kXP + C + c];
-        blk_fold(Xv, Ut, Lm, pI1, pJ1, ti, tj, si, sj, hc, hr, g, c, w0, w1, m0, m1);
-        acc[(R + g) * kXP + C + c] = m0;
-        acc[(R + g + 4) * kXP + C + c] = m1;
-      }
-    }
-    bar_compute();
-  }
+__device__ __forceinline__ void sts_if(bool p, uint32_t addr, E v) {
+  if constexpr (sizeof(E) == 4)
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.shared.u32 [%1], %2;\n\t}" ::"r"((uint32_t)p),
+                 "r"(addr), "r"(v)
+                 : "memory");
+  else
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.shared.u64 [%1], %2;\n\t}" ::"r"((uint32_t)p),
+                 "r"(addr), "l"(v)
+                 : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -308,7 +258,7 @@ __device__ __forceinline__ void for_each_segment(const McmTask& t, F&& body) {
 }
 
 template <bool I64>
-__global__ void __launch_bounds__(kMcmThreads, 3) mcm_main_kernel(const McmLaunchArgs a) {
+__global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(const McmLaunchArgs a) {
   using E = typename Cost<I64>::E;
   constexpr int KB = Cost<I64>::KB;
   using SM = Smem<I64>;
@@ -534,40 +484,110 @@ __global__ void __launch_bounds__(kMcmThreads, 3) mcm_main_kernel(const McmLaunc
             if (task.nparts > 0) cb[r] = umin(cb[r], finAcc[li * T + lane]);
           }
           if (D >= 1) {
-            E* Ut = reinterpret_cast<E*>(smem + SM::UT);
-            E* Lm = reinterpret_cast<E*>(smem + SM::LM);
-            E* accv = reinterpret_cast<E*>(smem + SM::ACCV);
-            E* pv = reinterpret_cast<E*>(smem + SM::PV);
-            for (int idx = tid; idx < T * T; idx += kComputeThreads) {
-              const int t = idx >> 5, x = idx & 31;
-              Ut[t * SM::UP + x] = finU[idx] >> shiftv;
-              Lm[t * SM::LP + x] = finL[idx] >> shiftv;
-            }
-            if (tid < T) {
-              pv[tid] = (E)finPP[tid];
-              pv[T + tid] = (E)(finPKI[tid] >> shiftv);
-              pv[2 * T + tid] = (E)(finPKJ[tid] >> shiftv);
-            }
+            E* Up = reinterpret_cast<E*>(smem + SM::WUP);
+            E* Lp = reinterpret_cast<E*>(smem + SM::WLP);
+            E* Xr = reinterpret_cast<E*>(smem + SM::WXR);
+            E* Xc = reinterpret_cast<E*>(smem + SM::WXC);
+            uint32_t* PKIp = reinterpret_cast<uint32_t*>(smem + SM::WPKI);
+            uint32_t* PKJp = reinterpret_cast<uint32_t*>(smem + SM::WPKJ);
+            constexpr E kInf = ~(E)0;
             // boundary split k = IT + 31: U[li][31] + m[IT+32][j] + w
             const E brow = finBrow[lane] >> shiftv;
             const E pI32 = (E)(finPKI[T - 1] >> shiftv);
-            E bnd[4];
+            E m[4], wv[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               const int li = 4 * w + r;
               bestS[li * T + lane] = cb[r];  // external minimum: (value, smallest k)
-              bnd[r] = (finU[(T - 1) * T + li] >> shiftv) + brow + pi[r] * pI32 * pj1;
-              accv[li * SM::XP + lane] = umin((E)(cb[r] >> KB), bnd[r]);
+              wv[r] = pi[r] * pj1;
+              const E bnd = (finU[(T - 1) * T + li] >> shiftv) + brow + wv[r] * pI32;
+              m[r] = umin((E)(cb[r] >> KB), bnd);
             }
+            for (int idx = tid; idx < SM::kRows * T; idx += kComputeThreads) {
+              const int q = idx >> 5, x = idx & 31, t = q - SM::kRowOff;
+              const bool in = t >= 0 && t <= T - 2;
+              Up[q * SM::UPW + x] = in ? (finU[t * T + x] >> shiftv) : (E)0;
+              Lp[idx] = in ? (finL[t * T + x] >> shiftv) : (E)0;
+            }
+            for (int idx = tid; idx < kDiagRows * T; idx += kComputeThreads) {
+              Xr[idx] = kInf;
+              Xc[idx] = kInf;
+            }
+            if (tid < SM::kRows) {
+              const int t = tid - SM::kRowOff;
+              const bool in = t >= 0 && t <= T - 2;
+              PKIp[tid] = in ? (finPKI[t] >> shiftv) : 0u;
+              PKJp[tid] = in ? (finPKJ[t] >> shiftv) : 0u;
+            }
+            const uint32_t sXr = smem_u32(Xr), sXc = smem_u32(Xc);
+            const int e_last = T - 2 - 4 * w;  // the warp's last cell, (4w, 31), is final after this step
+            const int e_row0 = -4 * w - 3;     // first step with a row operand in the warp's rows
+            const int c0 = lane - 4 * w - 1;   // at step e the lane's cell in row 4w + c0 - e becomes final
             bar_compute();
-            {
-              tile_solve_blocks<E>(Xv, accv, Ut, Lm, pv, pv + T, pv + 2 * T, warp, lane);
+            if (w == 7 && lane == 0) {  // cell (31, 0), the only cell of diagonal -31
+              Xr[T - 1] = m[3];
+              Xc[0] = m[3];
+            }
+            // Operands of the first step.  Window slot (u & 3) holds L[u][lane]
+            // and p[JT + u + 1] for u = 4w + e .. 4w + e + 3; with e = 1 mod 4
+            // at the start of each group of 4 steps, the slots are compile-time
+            // indices.
+            E R[4];
+            uint32_t P[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int u = 4 * w - (T - 1) + r;
+              R[(1 + r) & 3] = Lp[SM::row(u) * T + lane];
+              P[(1 + r) & 3] = PKJp[SM::row(u)];
+            }
+            Vec4<E> u4 = lds4(Up + SM::row(lane + T - 2) * SM::UPW + 4 * w);  // t = lane - 1 - e
+            E pkc = (E)PKIp[SM::row(lane + T - 2)];
+            bar_compute();
+#pragma unroll 1
+            for (int eb = -(T - 1); eb <= T - 2; eb += 4) {
+#pragma unroll
+              for (int s4 = 0; s4 < 4; ++s4) {
+                const int e = eb + s4;
+                if (e <= T - 2) {
+                  if (e <= e_last) {
+                    const int dI = e + T - 1;
+                    const E xc = Xc[dI * T + lane];             // column operand X[lane - e][lane]
+                    const Vec4<E> x4 = lds4(Xr + dI * T + 4 * w);  // row operands X[li][li + e]
+                    if (e >= e_row0) {
+#pragma unroll
+                      for (int r = 0; r < 4; ++r) {
+                        const int q = (1 + s4 + r) & 3;
+                        const E cc = u4.v[r] + xc + wv[r] * pkc;
+                        const E cr = x4.v[r] + R[q] + wv[r] * (E)P[q];
+                        m[r] = umin(m[r], umin(cc, cr));
+                      }
+                    } else {
+#pragma unroll
+                      for (int r = 0; r < 4; ++r) m[r] = umin(m[r], u4.v[r] + xc + wv[r] * pkc);
+                    }
+                    // the lane's cell on diagonal e + 1 is final now
+                    const int rr = c0 - e;
+                    const bool own = (unsigned)rr <= 3u;
+                    const E v = sel4(rr, m[0], m[1], m[2], m[3]);
+                    sts_if(own, sXr + (uint32_t)(((dI + 1) * T + 4 * w + rr) * (int)sizeof(E)), v);
+                    sts_if(own, sXc + (uint32_t)(((dI + 1) * T + lane) * (int)sizeof(E)), v);
+                    // operands of step e + 1 (independent of the tile values)
+                    const int un = 4 * w + e + 4;
+                    R[(1 + s4) & 3] = Lp[SM::row(un) * T + lane];
+                    P[(1 + s4) & 3] = PKJp[SM::row(un)];
+                    const int tn = lane - 2 - e;
+                    u4 = lds4(Up + SM::row(tn) * SM::UPW + 4 * w);
+                    pkc = (E)PKIp[SM::row(tn)];
+                  }
+                  bar_compute();
+                }
+              }
             }
             // ---------------- outputs needed by other tiles, then publish ----------------
             const int64_t nn = n;
             E vals[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) vals[r] = Xv[(4 * w + r) * SM::XP + lane];
+            for (int r = 0; r < 4; ++r) vals[r] = Xc[(lane - 4 * w - r + T - 1) * T + lane];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               const int li = 4 * w + r;
@@ -619,15 +639,42 @@ __global__ void __launch_bounds__(kMcmThreads, 3) mcm_main_kernel(const McmLaunc
               __threadfence();
               st_release(a.flags + tidx, 1);
             }
-            // provisional split: k of the external minimum (-1 if none); the split
-            // pass replaces it by the smallest k over all splits reaching the value
-#pragma unroll
+            // ---------------- split table (off the critical path) ----------------
+            // The smallest k reaching the final value, scanning in increasing
+            // k: column splits IT+li .. IT+30, the boundary IT+31, the
+            // external splits (smallest one kept with the external minimum),
+            // row splits JT .. j-1.
+            const unsigned long long kmask = (1ull << KB) - 1ull;
+#pragma unroll 1
             for (int r = 0; r < 4; ++r) {
               const int li = 4 * w + r;
               const int64_t i = IT + li, j = JT + lane;
-              const unsigned long long ek = bestS[li * T + lane];
-              const int kx = (ek >> KB) == (~0ull >> KB) ? -1 : (int)(ek & ((1ull << KB) - 1ull));
-              if (i < nn && j < nn) inst.s[i * nn + j] = (int16_t)kx;
+              if (i >= nn || j >= nn) continue;
+              // (register arrays are read through sel4: a runtime index would move them to local memory)
+              const E v = sel4(r, vals[0], vals[1], vals[2], vals[3]);
+              const E wr = sel4(r, wv[0], wv[1], wv[2], wv[3]);
+              int k = -1;
+              for (int t = li; t <= T - 2; ++t) {
+                if (Up[SM::row(t) * SM::UPW + li] + Xc[(lane - t - 1 + T - 1) * T + lane] + wr * (E)PKIp[SM::row(t)] ==
+                    v) {
+                  k = IT + t;
+                  break;
+                }
+              }
+              if (k < 0 && (finU[(T - 1) * T + li] >> shiftv) + brow + wr * pI32 == v) k = IT + T - 1;
+              if (k < 0) {
+                const unsigned long long ek = bestS[li * T + lane];
+                if ((E)(ek >> KB) == v) k = (int)(ek & kmask);
+              }
+              if (k < 0) {
+                for (int u = 0; u < lane; ++u) {
+                  if (Xr[(u - li + T - 1) * T + li] + Lp[SM::row(u) * T + lane] + wr * (E)PKJp[SM::row(u)] == v) {
+                    k = JT + u;
+                    break;
+                  }
+                }
+              }
+              inst.s[i * nn + j] = (int16_t)k;
             }
           } else {
             // diagonal tile: ordinary MCM on the 32-matrix sub-chain
@@ -798,70 +845,6 @@ __global__ void __launch_bounds__(256) mcm_prologue_kernel(const McmLaunchArgs a
   }
 }
 
-// Split pass for off-diagonal tiles: replaces the provisional split (k of
-// the smallest external candidate) by the smallest k over ALL splits whose
-// candidate equals the final m[i][j], scanning in increasing k: column splits
-// k = IT+li .. IT+30, the boundary split IT+31, the external split, the row
-// splits JT .. j-1.  Reads only the final table and the dims.
-template <bool I64>
-__global__ void __launch_bounds__(256) mcm_splits_kernel(const McmLaunchArgs a) {
-  using E = typename Cost<I64>::E;
-  __shared__ E Us[T][T + 1];   // Us[li][t]  = m[IT+li][IT+t]
-  __shared__ E Xs[T + 1][T + 1];  // Xs[r][lj] = m[IT+r][JT+lj], r = 0..32 (row 32: boundary row)
-  __shared__ E Ls[T][T + 1];   // Ls[u][lj] = m[JT+u+1][JT+lj]
-  __shared__ E pI[T + 1], pJ[T + 1];  // p[IT + x], p[JT + x + 1]
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  // after a device-reported error the tables (and provisional splits) were
-  // never written: touch nothing
-  if (*reinterpret_cast<volatile int32_t*>(a.status) != 0) return;
-  for (int t = blockIdx.x; t < a.ntasks; t += gridDim.x) {
-    const McmTask task = a.tasks[t];
-    const int I = task.I, J = task.J;
-    if (task.kind != 0 || J == I) continue;  // diagonal tiles compute exact splits themselves
-    const McmInstDev in = a.insts[task.inst];
-    const int64_t n = in.n;
-    const int IT = I * T, JT = J * T;
-    const E* m = static_cast<const E*>(in.m);
-    __syncthreads();
-    for (int idx = tid; idx < T * T; idx += blockDim.x) {
-      const int r = idx >> 5, x = idx & 31;
-      const int64_t gi = IT + r;
-      Us[r][x] = (gi < n && IT + x < n) ? m[gi * n + IT + x] : (E)0;
-      Xs[r][x] = (gi < n && JT + x < n) ? m[gi * n + JT + x] : (E)0;
-      const int64_t gl = JT + r + 1;
-      Ls[r][x] = (gl < n && JT + x < n) ? m[gl * n + JT + x] : (E)0;
-    }
-    if (tid < T) {
-      const int64_t gb = IT + T;
-      Xs[T][tid] = (gb < n && JT + tid < n) ? m[gb * n + JT + tid] : (E)0;
-    }
-    if (tid <= T) {
-      pI[tid] = (IT + tid <= n) ? (E)in.p[IT + tid] : (E)1;
-      pJ[tid] = (JT + tid + 1 <= n) ? (E)in.p[JT + tid + 1] : (E)1;
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int r = 0; r < 4; ++r) {
-      const int li = 4 * w + r;
-      const int64_t i = IT + li, j = JT + lane;
-      if (i >= n || j >= n) continue;
-      const E v = Xs[li][lane];
-      const E pij = pI[li] * pJ[lane];  // p[i] * p[j+1]
-      int k = -1;
-      for (int tt = li; tt <= T - 1 && k < 0; ++tt)  // column splits and (tt = 31) the boundary split
-        if (Us[li][tt] + Xs[tt + 1][lane] + pij * pI[tt + 1] == v) k = IT + tt;
-      if (k < 0) {
-        const int kx = in.s[i * n + j];  // external splits lie in [IT + 32, JT - 1]
-        if (kx >= IT + T && kx < JT && m[i * n + kx] + m[(int64_t)(kx + 1) * n + j] + pij * (E)in.p[kx + 1] == v)
-          k = kx;
-      }
-      for (int u = 0; u < lane && k < 0; ++u)
-        if (Xs[li][u] + Ls[u][lane] + pij * pJ[u] == v) k = JT + u;
-      in.s[i * n + j] = (int16_t)k;
-    }
-  }
-}
-
 }  // namespace
 
 size_t mcm_smem_bytes(bool i64) { return i64 ? Smem<true>::TOTAL : Smem<false>::TOTAL; }
@@ -887,12 +870,10 @@ cudaError_t mcm_preload(bool i64) {
   cudaError_t e;
   if (i64) {
     if ((e = cudaFuncGetAttributes(&fa, mcm_prologue_kernel<true>)) != cudaSuccess) return e;
-    if ((e = cudaFuncGetAttributes(&fa, mcm_main_kernel<true>)) != cudaSuccess) return e;
-    return cudaFuncGetAttributes(&fa, mcm_splits_kernel<true>);
+    return cudaFuncGetAttributes(&fa, mcm_main_kernel<true>);
   }
   if ((e = cudaFuncGetAttributes(&fa, mcm_prologue_kernel<false>)) != cudaSuccess) return e;
-  if ((e = cudaFuncGetAttributes(&fa, mcm_main_kernel<false>)) != cudaSuccess) return e;
-  return cudaFuncGetAttributes(&fa, mcm_splits_kernel<false>);
+  return cudaFuncGetAttributes(&fa, mcm_main_kernel<false>);
 }
 
 cudaError_t launch_mcm_prologue(const McmLaunchArgs& a, bool i64, cudaStream_t st) {
@@ -901,15 +882,6 @@ cudaError_t launch_mcm_prologue(const McmLaunchArgs& a, bool i64, cudaStream_t s
     mcm_prologue_kernel<true><<<a.ninst, 256, 0, st>>>(a);
   else
     mcm_prologue_kernel<false><<<a.ninst, 256, 0, st>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_mcm_splits(const McmLaunchArgs& a, bool i64, int grid, cudaStream_t st) {
-  if (a.ntasks <= 0) return cudaSuccess;
-  if (i64)
-    mcm_splits_kernel<true><<<grid, 256, 0, st>>>(a);
-  else
-    mcm_splits_kernel<false><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -26,9 +26,7 @@
 // Tasks are popped from one queue in order of the tile-diagonal at which they
 // become ready (finishers of diagonal D after every task they wait for), so a
 // block only ever waits for tasks popped before its own: the queue makes
-// progress whatever the number of resident blocks.  The smallest minimising
-// split of an off-diagonal tile is recovered afterwards by a separate pass
-// (mcm_splits_kernel) from the final table, off the critical path.
+// progress whatever the number of resident blocks.
 //
 // Cost encodings (exact integer arithmetic throughout):
 //   int32 costs: every candidate is at most (n-1)*max(p)^3 =: bound < 2^31.
@@ -111,7 +109,6 @@ cudaError_t mcm_configure(bool i64);
 cudaError_t mcm_occupancy(bool i64, int* blocks_per_sm);
 cudaError_t launch_mcm_prologue(const McmLaunchArgs& a, bool i64, cudaStream_t st);
 cudaError_t launch_mcm_main(const McmLaunchArgs& a, bool i64, int grid, cudaStream_t st);
-cudaError_t launch_mcm_splits(const McmLaunchArgs& a, bool i64, int grid, cudaStream_t st);
 // Loads the prologue, main and split-pass kernels into the current context
 // (with lazy module loading a kernel is otherwise loaded at its first launch).
 cudaError_t mcm_preload(bool i64);

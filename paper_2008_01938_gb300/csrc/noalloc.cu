@@ -12,8 +12,8 @@
 // loaded, and everything a solve needs inside it -- the work queue included
 // -- is written by a set-up kernel at the start of each call.
 //
-// The kernels that solve are the ones mcm_solve runs (prologue, persistent
-// main kernel, split pass); only the way their arguments are laid out
+// The kernels that solve are the ones mcm_solve runs (prologue and
+// persistent main kernel); only the way their arguments are laid out
 // differs.  The paper has no counterpart to this entry point.
 #include <cuda_runtime.h>
 
@@ -292,7 +292,5 @@ extern "C" dp_status mcm_solve_noalloc(const int32_t* p, int32_t n, int32_t* m, 
   const int grid = (int)std::max<int64_t>(2, std::min<int64_t>((int64_t)d.sms * d.occ, ntasks));
   if ((e = dpk::launch_mcm_main(a, false, grid, st)) != cudaSuccess)
     return dph::fail_cuda(e, "mcm_solve_noalloc: launch MCM kernel");
-  if ((e = dpk::launch_mcm_splits(a, false, d.sms * 8, st)) != cudaSuccess)
-    return dph::fail_cuda(e, "mcm_solve_noalloc: launch split pass");
   return DP_OK;
 }

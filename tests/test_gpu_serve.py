@@ -1,0 +1,118 @@
+"""Continuous-batching server: every result served in a mix of concurrent
+MCM and S-DP requests equals the same request solved alone (bit-exact),
+small ones equal the oracle, and admission refuses work beyond the HBM cap."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_01938_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dp():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2008_01938_gb300 as dp
+    return dp
+
+
+def _alone(dp, r, cost):
+    import torch
+    if r.kind == "mcm":
+        m, s = dp.mcm_solve(torch.from_numpy(r.dims).cuda(), cost=cost)
+        dp.sync_status()
+        return m.cpu().numpy(), s.cpu().numpy()
+    st = np.zeros(max(r.n, int(r.offsets[0])), dtype=np.uint32)
+    st[: r.offsets[0]] = r.preset
+    t = torch.from_numpy(st.view(np.int32)).cuda()
+    dp.sdp_solve(t, r.offsets, op="min", n=r.n)
+    dp.sync_status()
+    return t.cpu().numpy().view(np.uint32)[: r.n]
+
+
+def _serve_all(dp, trace, costs, **cfg):
+    import time
+    srv = dp.Server(**cfg)
+    tickets = []
+    for r, c in zip(trace, costs):
+        tk = srv.submit_mcm(r.dims, cost=c) if r.kind == "mcm" else srv.submit_sdp(r.n, r.offsets, r.preset)
+        assert tk is not None
+        tickets.append(tk)
+    out = {}
+    t_end = time.time() + 120
+    while len(out) < len(tickets):
+        assert time.time() < t_end, "server did not finish"
+        for tk, r, c in zip(tickets, trace, costs):
+            if tk in out:
+                continue
+            res = srv.poll(tk)
+            if res is None:
+                continue
+            assert res.status == 0, f"request failed with status {res.status}"
+            assert res.t_submit <= res.t_start <= res.t_done
+            if r.kind == "mcm":
+                m, s = srv.tables(res, cost=c)
+                out[tk] = (m.cpu().numpy(), s.cpu().numpy())
+            else:
+                out[tk] = srv.tables(res).cpu().numpy().view(np.uint32)[: r.n].copy()
+            srv.release(tk)
+        time.sleep(1e-3)
+    srv.close()
+    return [out[tk] for tk in tickets]
+
+
+def test_mix_equals_alone(dp):
+    trace = inputs.serve_trace(rate=2000.0, duration=1.0, seed=11, mcm_n=(16, 700), sdp_n=(1 << 16, 1 << 18),
+                               max_requests=48)
+    assert sum(r.kind == "sdp" for r in trace) >= 3 and sum(r.kind == "mcm" for r in trace) >= 20
+    # mostly int64 like the serving mix, every fourth MCM request int32 (dims kept small enough)
+    costs = []
+    for i, r in enumerate(trace):
+        if r.kind == "mcm" and i % 4 == 0:
+            r.dims = np.minimum(r.dims, 40).astype(np.int32)
+            costs.append("i32")
+        else:
+            costs.append("i64")
+    served = _serve_all(dp, trace, costs, hbm_cap_bytes=8 << 30, max_inflight=1000, num_streams=4, max_batch=16)
+    for r, c, got in zip(trace, costs, served):
+        want = _alone(dp, r, c)
+        if r.kind == "mcm":
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1]), f"MCM n={r.n} differs"
+        else:
+            assert np.array_equal(got, want), f"S-DP n={r.n} differs"
+    # the small MCM requests also against the oracle
+    checked = 0
+    for r, got in zip(trace, served):
+        if r.kind == "mcm" and r.n <= 200:
+            om, os_ = oracle.mcm(r.dims)
+            assert np.array_equal(got[0].astype(np.int64), om) and np.array_equal(got[1], os_)
+            checked += 1
+    assert checked >= 3
+
+
+def test_admission_by_footprint(dp):
+    # an int64 request of n = 600 accounts for about 11.8 MB (tables and
+    # workspace): one fits under a 16 MiB cap, two do not
+    srv = dp.Server(hbm_cap_bytes=16 << 20, max_inflight=8, num_streams=2, max_batch=4)
+    d = inputs.mcm_dims(600, 1, 1000, seed=12)
+    t1 = srv.submit_mcm(d)
+    assert t1 is not None
+    assert srv.submit_mcm(d) is None
+    import time
+    t_end = time.time() + 60
+    while srv.poll(t1) is None:
+        assert time.time() < t_end
+        time.sleep(1e-3)
+    srv.release(t1)                                   # its HBM returns to admission
+    t2 = srv.submit_mcm(d)
+    assert t2 is not None
+    while srv.poll(t2) is None:
+        assert time.time() < t_end
+        time.sleep(1e-3)
+    m, s = srv.tables(srv.poll(t2))
+    om, _ = oracle.mcm(d)
+    assert int(m[0, -1].item()) == int(om[0, -1])
+    srv.release(t2)
+    srv.close()
