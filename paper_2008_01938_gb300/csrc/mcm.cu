@@ -39,6 +39,10 @@ struct Smem {
   static constexpr int ES = I64 ? 8 : 4;
   static constexpr int TILE = T * T * ES;
   static constexpr bool kPadRows = !I64;
+  // int32: the cell-value arrays Xr / Xc live outside the stage area, so
+  // their entries for cells that do not exist are set to all ones once per
+  // block and stay so (every existing cell is written before it is read).
+  static constexpr bool kXOut = !I64;
   static constexpr int kRows = kPadRows ? 96 : 64;
   static constexpr int kRowOff = kPadRows ? 32 : 0;
   static constexpr int UPW = I64 ? 34 : 36;                       // U^T pitch: 16-byte rows, conflict-free
@@ -47,13 +51,13 @@ struct Smem {
   static constexpr int STB = STA + 4 * TILE;                     // [group][stage] column panels
   static constexpr int STPK = STB + 4 * TILE;                    // [group][stage] 32 x u32 dims
   static constexpr int STEND = STPK + 4 * 128;
+  static constexpr int XBYTES = kDiagRows * T * ES;
   static constexpr int WUP = STA;                                // Up[row(t)][li] = m[IT+li][IT+t]
   static constexpr int WLP = WUP + ((kRows * UPW * ES + 127) / 128) * 128;  // Lp[row(u)][lj] = m[JT+u+1][JT+lj]
-  static constexpr int WXR = WLP + kRows * T * ES;               // Xr[e+31][li]: final value of cell (li, li+e)
-  static constexpr int WXC = WXR + kDiagRows * T * ES;           // Xc[e+31][lj]: final value of cell (lj-e, lj)
-  static constexpr int WPKI = WXC + kDiagRows * T * ES;          // PKIp[row(t)] = p[IT+t+1]
+  static constexpr int WPKI = WLP + kRows * T * ES;               // PKIp[row(t)] = p[IT+t+1]
   static constexpr int WPKJ = WPKI + kRows * 4;                  // PKJp[row(u)] = p[JT+u+1]
-  static constexpr int WEND = WPKJ + kRows * 4;
+  static constexpr int WXIN = (WPKJ + kRows * 4 + 127) / 128 * 128;  // Xr, Xc when inside the stage area
+  static constexpr int WEND = kXOut ? WXIN : WXIN + 2 * XBYTES;
   static constexpr int FINU = ((STEND > WEND ? STEND : WEND) + 127) / 128 * 128;  // row panel of (I,I)
   static constexpr int FINL = FINU + TILE;                       // column panel of diagonal tile (J,J)
   static constexpr int FINBROW = FINL + TILE;                    // boundary row (one tile row)
@@ -62,7 +66,9 @@ struct Smem {
   static constexpr int FINPKJ = FINPKI + 128;                    // p[32J+1 ..] << S
   static constexpr int FINACC = FINPKJ + 128;                    // bulk-task partial minima
   static constexpr int BEST = FINACC + T * T * 8;                // running (value, k) keys
-  static constexpr int TOTAL = BEST + T * T * 8;
+  static constexpr int WXR = kXOut ? BEST + T * T * 8 : WXIN;    // Xr[e+31][li]: final value of cell (li, li+e)
+  static constexpr int WXC = WXR + XBYTES;                       // Xc[e+31][lj]: final value of cell (lj-e, lj)
+  static constexpr int TOTAL = kXOut ? WXC + XBYTES : BEST + T * T * 8;
   static constexpr int XV = STA;                                 // diagonal tiles: the tile's values
   __host__ __device__ static constexpr int row(int t) { return kPadRows ? t + kRowOff : (t & 63); }
   static_assert(WXR % 16 == 0 && WUP % 16 == 0 && (UPW * ES) % 16 == 0, "16-byte vector rows");
@@ -145,24 +151,25 @@ __device__ __forceinline__ Vec4<E> lds4(const E* p) {  // 4 consecutive elements
   return r;
 }
 
-// a[r] for a runtime r in 0..3 as a chain of predicated selects (a C
-// conditional chain here is compiled to divergent branches, which cost
-// several times more inside the wavefront step).
+// a[r] for a runtime r in 0..3 (any r: only its low two bits are used) as
+// a two-level tree of predicated selects (a C conditional chain here is
+// compiled to divergent branches, which cost several times more inside the
+// wavefront step).
 template <typename E>
 __device__ __forceinline__ E sel4(int r, E a0, E a1, E a2, E a3) {
   if constexpr (sizeof(E) == 4) {
     uint32_t v;
-    asm("{\n\t.reg .pred p1, p2, p3;\n\t"
-        "setp.eq.s32 p1, %5, 1;\n\tsetp.eq.s32 p2, %5, 2;\n\tsetp.eq.s32 p3, %5, 3;\n\t"
-        "selp.b32 %0, %2, %1, p1;\n\tselp.b32 %0, %3, %0, p2;\n\tselp.b32 %0, %4, %0, p3;\n\t}"
+    asm("{\n\t.reg .pred p0, p1;\n\t.reg .b32 lo, hi, b;\n\t"
+        "and.b32 b, %5, 1;\n\tsetp.ne.u32 p0, b, 0;\n\tand.b32 b, %5, 2;\n\tsetp.ne.u32 p1, b, 0;\n\t"
+        "selp.b32 lo, %2, %1, p0;\n\tselp.b32 hi, %4, %3, p0;\n\tselp.b32 %0, hi, lo, p1;\n\t}"
         : "=r"(v)
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(r));
     return v;
   } else {
     unsigned long long v;
-    asm("{\n\t.reg .pred p1, p2, p3;\n\t"
-        "setp.eq.s32 p1, %5, 1;\n\tsetp.eq.s32 p2, %5, 2;\n\tsetp.eq.s32 p3, %5, 3;\n\t"
-        "selp.b64 %0, %2, %1, p1;\n\tselp.b64 %0, %3, %0, p2;\n\tselp.b64 %0, %4, %0, p3;\n\t}"
+    asm("{\n\t.reg .pred p0, p1;\n\t.reg .b64 lo, hi;\n\t.reg .b32 b;\n\t"
+        "and.b32 b, %5, 1;\n\tsetp.ne.u32 p0, b, 0;\n\tand.b32 b, %5, 2;\n\tsetp.ne.u32 p1, b, 0;\n\t"
+        "selp.b64 lo, %2, %1, p0;\n\tselp.b64 hi, %4, %3, p0;\n\tselp.b64 %0, hi, lo, p1;\n\t}"
         : "=l"(v)
         : "l"(a0), "l"(a1), "l"(a2), "l"(a3), "r"(r));
     return v;
@@ -286,6 +293,10 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
   const long long limit = a.spin_limit;
   int32_t* status = a.status;
 
+  if constexpr (SM::kXOut) {
+    E* x = reinterpret_cast<E*>(smem + SM::WXR);
+    for (int i = tid; i < 2 * kDiagRows * T; i += blockDim.x) x[i] = ~(E)0;
+  }
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) {
       mbar_init(&bar_full[i], 1);
@@ -509,9 +520,11 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
               Up[q * SM::UPW + x] = in ? (finU[t * T + x] >> shiftv) : (E)0;
               Lp[idx] = in ? (finL[t * T + x] >> shiftv) : (E)0;
             }
-            for (int idx = tid; idx < kDiagRows * T; idx += kComputeThreads) {
-              Xr[idx] = kInf;
-              Xc[idx] = kInf;
+            if constexpr (!SM::kXOut) {
+              for (int idx = tid; idx < kDiagRows * T; idx += kComputeThreads) {
+                Xr[idx] = kInf;
+                Xc[idx] = kInf;
+              }
             }
             if (tid < SM::kRows) {
               const int t = tid - SM::kRowOff;
@@ -521,7 +534,6 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
             }
             const uint32_t sXr = smem_u32(Xr), sXc = smem_u32(Xc);
             const int e_last = T - 2 - 4 * w;  // the warp's last cell, (4w, 31), is final after this step
-            const int e_row0 = -4 * w - 3;     // first step with a row operand in the warp's rows
             const int c0 = lane - 4 * w - 1;   // at step e the lane's cell in row 4w + c0 - e becomes final
             bar_compute();
             if (w == 7 && lane == 0) {  // cell (31, 0), the only cell of diagonal -31
@@ -553,17 +565,12 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
                     const int dI = e + T - 1;
                     const E xc = Xc[dI * T + lane];             // column operand X[lane - e][lane]
                     const Vec4<E> x4 = lds4(Xr + dI * T + 4 * w);  // row operands X[li][li + e]
-                    if (e >= e_row0) {
 #pragma unroll
-                      for (int r = 0; r < 4; ++r) {
-                        const int q = (1 + s4 + r) & 3;
-                        const E cc = u4.v[r] + xc + wv[r] * pkc;
-                        const E cr = x4.v[r] + R[q] + wv[r] * (E)P[q];
-                        m[r] = umin(m[r], umin(cc, cr));
-                      }
-                    } else {
-#pragma unroll
-                      for (int r = 0; r < 4; ++r) m[r] = umin(m[r], u4.v[r] + xc + wv[r] * pkc);
+                    for (int r = 0; r < 4; ++r) {
+                      const int q = (1 + s4 + r) & 3;
+                      const E cc = u4.v[r] + xc + wv[r] * pkc;
+                      const E cr = x4.v[r] + R[q] + wv[r] * (E)P[q];
+                      m[r] = umin(m[r], umin(cc, cr));
                     }
                     // the lane's cell on diagonal e + 1 is final now
                     const int rr = c0 - e;
@@ -583,30 +590,11 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
                 }
               }
             }
-            // ---------------- outputs needed by other tiles, then publish ----------------
+            // ---------------- panels needed by other tiles, then publish ----------------
             const int64_t nn = n;
             E vals[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) vals[r] = Xc[(lane - 4 * w - r + T - 1) * T + lane];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              const int li = 4 * w + r;
-              const int64_t i = IT + li, j = JT + lane;
-              if (i < nn && j < nn) {
-                if constexpr (I64)
-                  static_cast<int64_t*>(inst.m)[i * nn + j] = (int64_t)vals[r];
-                else
-                  static_cast<int32_t*>(inst.m)[i * nn + j] = (int32_t)vals[r];
-              }
-              const int64_t i2 = JT + li, j2 = IT + lane;  // mirror tile (J, I)
-              if (i2 < nn && j2 < nn) {
-                if constexpr (I64)
-                  static_cast<int64_t*>(inst.m)[i2 * nn + j2] = 0;
-                else
-                  static_cast<int32_t*>(inst.m)[i2 * nn + j2] = 0;
-                inst.s[i2 * nn + j2] = -1;
-              }
-            }
             {
               E* af = static_cast<E*>(a.af) + tidx * T * T;
               E pa[4];
@@ -638,6 +626,26 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
             if (tid == 0) {
               __threadfence();
               st_release(a.flags + tidx, 1);
+            }
+            // ---------------- the tables themselves (not read by other tiles) ----------------
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int li = 4 * w + r;
+              const int64_t i = IT + li, j = JT + lane;
+              if (i < nn && j < nn) {
+                if constexpr (I64)
+                  static_cast<int64_t*>(inst.m)[i * nn + j] = (int64_t)vals[r];
+                else
+                  static_cast<int32_t*>(inst.m)[i * nn + j] = (int32_t)vals[r];
+              }
+              const int64_t i2 = JT + li, j2 = IT + lane;  // mirror tile (J, I)
+              if (i2 < nn && j2 < nn) {
+                if constexpr (I64)
+                  static_cast<int64_t*>(inst.m)[i2 * nn + j2] = 0;
+                else
+                  static_cast<int32_t*>(inst.m)[i2 * nn + j2] = 0;
+                inst.s[i2 * nn + j2] = -1;
+              }
             }
             // ---------------- split table (off the critical path) ----------------
             // The smallest k reaching the final value, scanning in increasing
