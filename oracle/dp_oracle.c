@@ -35,7 +35,7 @@
  *     m[i][j] = min over i <= k < j of  m[i][k] + m[k+1][j] + p[i]*p[k+1]*p[j+1]
  *     s[i][j] = the smallest k attaining that minimum.
  * Cells are filled diagonal by diagonal (d = j - i = 1 .. n-1), which is the
- * computation order of the paper's Fig. 4; k runs upward and only a strictly
+ * computation order of the paper's Fig. 5; k runs upward and only a strictly
  * smaller candidate replaces the current best, so ties keep the smaller k.
  * Every candidate is formed in int64; ORACLE_EOVERFLOW if one does not fit.
  */

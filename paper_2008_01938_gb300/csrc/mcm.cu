@@ -108,7 +108,7 @@ __device__ __forceinline__ E umin(E a, E b) { return a < b ? a : b; }
 //
 // Cell (li, lj) lies on cell diagonal e = lj - li in [-31, 31] and depends
 // only on cells of lower diagonals, so the tile is solved in the paper's
-// diagonal order (Figs. 4-6), one diagonal per step: in step e every cell
+// diagonal order (Figs. 5-7), one diagonal per step: in step e every cell
 // pulls the candidate of its row split and of its column split whose operand
 // lies on diagonal e (exactly one of each), and the cells of diagonal e + 1,
 // whose last operands were on diagonal e, become final.  Warp w owns rows

@@ -15,7 +15,7 @@
 //   * the boundary split k = 32I + 31 (needs row 32(I+1) of tile (I+1, J));
 //   * the in-tile splits k in [i, 32I+30] and [32J, j-1], which depend on the
 //     tile's own cells and are resolved by a wavefront over the tile's 63
-//     anti-diagonals (the paper's diagonal computation order, Figs. 4-6,
+//     anti-diagonals (the paper's diagonal computation order, Figs. 5-7,
 //     applied inside one tile).
 // Work items ("tasks") are (tile, range of r levels).  A bulk task reduces a
 // group of external segments and merges its (value, k) minima into the tile's
