@@ -140,6 +140,25 @@ def _profile_traffic():
     return float(mbytes.group(1))
 
 
+def max_over_ranks(ms, device=None):
+    """The largest per-rank step time (ms) over the process group; the local
+    value when no group is initialised.  Replicas of the solve run one per
+    rank with no exchange, so this is the only collective of the benchmark."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, ms, evals=EVALS_4096):
+    """Whole-job split-evals/s of `world` replicas that each solved one chain
+    in at most `ms` milliseconds."""
+    return world * evals / (ms / 1e3)
+
+
 def _cpu_baseline(n_sample=2048):
     import oracle
     from paper_2008_01938_gb300 import inputs
@@ -208,14 +227,9 @@ def run_gb300(args):
     t_wall1 = time.time()
     dp.sync_status()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(statistics.mean(step_ms), device=dev)
     clocks = sampler.stop(t_wall0, t_wall1)
-    value = world * EVALS_4096 / (ms / 1e3)
+    value = replica_throughput(world, ms)
     kernel_ms = kms.value / max(kn.value, 1)
 
     # correctness spot check of the timed output (cheap: final cell + digest)
