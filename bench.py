@@ -279,15 +279,19 @@ def run_gb300(args):
         "config": {"workload": "MCM n=4096 chain, dims U[1,32] seed 1, int32 m + int16 s, one mcm_solve per step",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 2 * args.steps,
         "clocks": clocks, "e2e": e2e, "roofline": roof, "parity_sha256_ok": parity,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = _cpu_baseline()
     if world == 1 and not args.no_extras:
-        out["sdp"] = bench_sdp(dp, native, lib, dev, args)
-        out["batched"] = bench_batched(dp, native, lib, dev, args)
-        out["serve"] = bench_serve(dp, native, dev, args)
+        extras = set(args.extras.split(","))
+        if "sdp" in extras:
+            out["sdp"] = bench_sdp(dp, native, lib, dev, args)
+        if "batched" in extras:
+            out["batched"] = bench_batched(dp, native, lib, dev, args)
+        if "serve" in extras:
+            out["serve"] = bench_serve(dp, native, dev, args)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -499,6 +503,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extras", default="sdp,batched,serve",
+                    help="comma-separated sections after the headline: sdp, batched, serve")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     args = ap.parse_args()
