@@ -327,10 +327,16 @@ def bench_sdp(dp, native, lib, dev, args):
         kms = c.value / max(d.value, 1)
         cells = big.n - a1
         bytes_ = 4 * cells + 4 * a1
+        k = int(big.offsets.size)
+        smem_peak = 32 * SM_MAX_MHZ * 1e6 / 1e9   # one SM: 32 shared-memory words per clock, G words/s
         res[op] = {"cells_per_s": cells / (kms / 1e3), "kernel_ms": kms, "wall_ms": wall * 1e3,
                    "roofline": {"bound": "hbm", "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm,
                                 "unit": "GB/s", "frac": bytes_ / (kms / 1e3) / 1e9 / hbm,
-                                "note": "dependency chain of (n-a_1)/a_k steps bounds it, not HBM"}}
+                                "note": "dependency chain of (n-a_1)/a_k steps bounds it, not HBM"},
+                   "smem_roofline": {"bound": "shared memory of the one SM the chain runs on",
+                                     "achieved": cells * k / (kms / 1e3) / 1e9, "peak": smem_peak,
+                                     "unit": "G words/s", "frac": cells * k / (kms / 1e3) / 1e9 / smem_peak,
+                                     "per_unit": f"{k} window reads per cell"}}
     return res
 
 

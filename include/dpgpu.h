@@ -158,7 +158,9 @@ dp_status mcm_plan_destroy(void *plan);
 /* Fills ST[a_1 .. n-1] in place.
  *   ST      device uint32[n]; ST[0 .. a[0]-1] must hold the preset values.
  *   n       table length (n <= a[0] is a no-op returning DP_OK).
- *   a       HOST int32[k], strictly decreasing, a[k-1] >= 1, a[0] <= 65536.
+ *   a       HOST int32[k], strictly decreasing, a[k-1] >= 1 (any a[0]: windows of
+ *           up to 32768 words are kept in shared memory, larger ones are read
+ *           from the table in global memory).
  *   op      DP_OP_MIN or DP_OP_ADD_MOD32.
  * Both operators are commutative and associative, so the result does not
  * depend on the order in which the k terms are combined. */

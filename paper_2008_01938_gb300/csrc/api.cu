@@ -380,6 +380,7 @@ struct SdpPlan {
   int32_t batch = 0;
   int op = 0;
   int threads = 32, ring_log2 = 0, kmax = 1;
+  bool kfull = false;
   dpk::SdpInstDev* d_insts = nullptr;
   int32_t* d_offs = nullptr;
 };
@@ -574,6 +575,7 @@ dp_status sdp_solve(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, dp_op 
   args.one.n = n;
   args.one.a = nullptr;
   args.one.k = k;
+  args.kfull = k == dpk::kSdpMaxKRegs;
   args.ninst = 1;
   args.op = (int32_t)op;
   sdp_shape(a[0], a[k - 1], &args.threads, &args.ring_log2);
@@ -617,9 +619,10 @@ dp_status sdp_plan_create(int32_t batch, const int64_t* n_host, const int32_t* k
   std::vector<dpk::SdpInstDev> insts((size_t)batch);
   int64_t aoff = 0;
   int kmax = 1, threads = 32, ring_log2 = 1;
-  bool ring_ok = true;
+  bool ring_ok = true, kfull = batch > 0;
   for (int b = 0; b < batch; ++b) {
     const int32_t* a = a_host + aoff;
+    kfull = kfull && k_host[b] == dpk::kSdpMaxKRegs;
     if ((rc = sdp_validate(n_host[b], a, k_host[b], op)) != DP_OK) return fail(rc, "instance %d: %s", b, t_err.c_str());
     insts[b].n = n_host[b];
     insts[b].k = k_host[b];
@@ -646,6 +649,7 @@ dp_status sdp_plan_create(int32_t batch, const int64_t* n_host, const int32_t* k
   pl->threads = threads;
   pl->ring_log2 = ring_ok ? ring_log2 : 0;
   pl->kmax = kmax;
+  pl->kfull = kfull;
   cudaError_t e;
   if ((e = cudaMalloc(&pl->d_offs, std::max<int64_t>(aoff, 4) * 4)) != cudaSuccess ||
       (e = cudaMalloc(&pl->d_insts, std::max<size_t>(insts.size(), 1) * sizeof(dpk::SdpInstDev))) != cudaSuccess) {
@@ -677,6 +681,7 @@ dp_status sdp_solve_batched(void* plan, uint32_t* ST_all, const int64_t* st_off,
   dpk::SdpLaunchArgs args{};
   args.insts = pl->d_insts;
   args.one.k = pl->kmax;
+  args.kfull = pl->kfull;
   args.ninst = pl->batch;
   args.op = pl->op;
   args.threads = pl->threads;

@@ -200,7 +200,7 @@ dp_status launch_mcm_group(Server* S, const std::vector<Req*>& reqs, bool i64, L
 
 dp_status launch_sdp_group(Server* S, const std::vector<Req*>& reqs, int op, Launch* L) {
   int threads = 32, kmax = 1, ring_log2 = 1;
-  bool ring_ok = true;
+  bool ring_ok = true, kfull = !reqs.empty();
   std::vector<int64_t> st_off(reqs.size());
   int64_t cells = 0, noffs = 0;
   for (size_t b = 0; b < reqs.size(); ++b) {
@@ -208,6 +208,7 @@ dp_status launch_sdp_group(Server* S, const std::vector<Req*>& reqs, int op, Lau
     st_off[b] = cells;
     cells = (int64_t)align_up((size_t)(cells + std::max<int64_t>(r->n, r->offs[0])), 64);
     kmax = std::max(kmax, (int)r->offs.size());
+    kfull = kfull && (int)r->offs.size() == dpk::kSdpMaxKRegs;
     int th, lg;
     sdp_shape(r->offs[0], r->offs.back(), &th, &lg);
     threads = std::max(threads, th);
@@ -271,6 +272,7 @@ dp_status launch_sdp_group(Server* S, const std::vector<Req*>& reqs, int op, Lau
   dpk::SdpLaunchArgs args{};
   args.insts = reinterpret_cast<const dpk::SdpInstDev*>(ws + o_insts);
   args.one.k = kmax;
+  args.kfull = kfull;
   args.ninst = (int32_t)reqs.size();
   args.op = op;
   args.threads = threads;
