@@ -106,7 +106,7 @@ dp_status mcm_solve(const int32_t *p, int32_t n, dp_cost ct, void *m, int16_t *s
  * latency-critical loop that must not enter an allocator.
  *   p, n, m, s  as for mcm_solve with ct = DP_COST_I32; m is int32[n*n].
  *   n           1 <= n <= 1024: the scratch is a fixed file-scope device
- *               array of 8,708,864 bytes per device; a larger n returns
+ *               array of 8,691,968 bytes per device; a larger n returns
  *               DP_EINVAL without touching the device.
  *   status_dev  required (NULL is DP_EINVAL): caller-owned device int32 that
  *               is zero on entry; device-side errors land there, read them

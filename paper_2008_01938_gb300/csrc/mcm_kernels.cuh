@@ -54,7 +54,7 @@ constexpr int kStages = 2;                             // bulk-copy stages per g
 // r = (D+1)/2 .. D-1 go to bulk tasks of kLevelsPerPart levels each, except
 // the last level, which the finisher keeps; a tile with fewer than
 // kMinBulkLevels bulk levels is not split at all.
-constexpr int kLevelsPerPart = 4;
+constexpr int kLevelsPerPart = 8;
 constexpr int kMinBulkLevels = 2;
 
 struct McmInstDev {

@@ -53,7 +53,7 @@ constexpr int64_t kPK = kPP + align256(((int64_t)kMaxNt * kTile + 32) * 4);
 constexpr int64_t kInsts = kPK + align256((int64_t)kMaxNt * kTile * 4);
 constexpr int64_t kTasks = kInsts + 256;
 constexpr int64_t kAccSlot = kTasks + align256(kMaxTasks * (int64_t)sizeof(McmTask));
-constexpr int64_t kScratchBytes = kAccSlot + align256(kMaxTiles * 4);  // about 8.3 MiB
+constexpr int64_t kScratchBytes = kAccSlot + align256(kMaxTiles * 4);  // 8,691,968 bytes
 
 static_assert(sizeof(McmInstDev) <= 256, "chain record must fit its region");
 static_assert(sizeof(McmTask) == 16, "task layout");
