@@ -119,7 +119,8 @@ __device__ __forceinline__ void set_status(int32_t* status, int32_t code) {
   atomicCAS(status, 0, code);
 }
 
-// Spins until *flag >= target (relaxed polling, then one acquire fence).
+// Spins until *flag >= target (relaxed polling with a short sleep -- a waiting
+// finisher is usually on the critical path -- then one acquire fence).
 // Returns false (and records DP_ETIMEOUT) if `limit` cycles pass first or if
 // another block already recorded an error.
 __device__ __forceinline__ bool wait_flag_geq(const int32_t* flag, int32_t target, long long limit,
@@ -138,7 +139,7 @@ __device__ __forceinline__ bool wait_flag_geq(const int32_t* flag, int32_t targe
     }
     if (*reinterpret_cast<volatile const int32_t*>(status) != 0) return false;
     __nanosleep(backoff);
-    backoff = backoff < 256 ? backoff * 2 : 256;
+    backoff = backoff < 64 ? backoff * 2 : 64;
   }
 }
 

@@ -623,10 +623,9 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
               }
             }
             bar_compute();
-            if (tid == 0) {
-              __threadfence();
-              st_release(a.flags + tidx, 1);
-            }
+            // release: the panel stores of every compute thread, ordered before
+            // this store by the barrier, are visible to whoever acquires the flag
+            if (tid == 0) st_release(a.flags + tidx, 1);
             // ---------------- the tables themselves (not read by other tiles) ----------------
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -777,7 +776,7 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
     if (finisher) ++fin_cnt;
     __syncthreads();
     if (tid == 0 && *reinterpret_cast<volatile int32_t*>(status) == 0) {
-      __threadfence();
+      // release (cumulative over the block's merges and stores before the barrier)
       if (!finisher)
         red_release_add(a.counters + tidx, 1);
       else if (D == 0)  // off-diagonal tiles publish right after their values
