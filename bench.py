@@ -354,7 +354,7 @@ def bench_batched(dp, native, lib, dev, args):
     s_all = torch.empty(int(b.tab_off[-1]), dtype=torch.int16, device=dev)
     st = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(st):
-        plan.solve(p_all, p_off, tab_off, m_all, s_all, stream=st)
+        tuned = plan.autotune(p_all, p_off, tab_off, m_all, s_all, stream=st)
     st.synchronize()
     dp.sync_status()
     g = torch.cuda.CUDAGraph()
@@ -395,7 +395,8 @@ def bench_batched(dp, native, lib, dev, args):
     return {"workload": "10,000 chains, n log-uniform [8,512], dims U[1,1000] seed 3, int64 costs",
             "split_evals": total, "graph_evals_per_s": total / t_graph, "graph_ms": t_graph * 1e3,
             "plain_loop_evals_per_s": total / t_plain, "plain_loop_ms": t_plain * 1e3,
-            "speedup_vs_plain": t_plain / t_graph, "parity_sha256_ok": parity}
+            "speedup_vs_plain": t_plain / t_graph, "parity_sha256_ok": parity,
+            "autotuned": {"levels_per_bulk_task": tuned[0], "blocks_per_sm": tuned[1]}}
 
 
 def bench_serve(dp, native, dev, args):

@@ -149,6 +149,23 @@ dp_status mcm_solve_batched(void *plan, const int32_t *p_all, const int64_t *p_o
                             const int64_t *tab_off, void *m_all, int16_t *s_all,
                             int32_t *status_dev, void *stream);
 
+/* Autotuner for a plan: runs the plan on the caller's own buffers (as for
+ * mcm_solve_batched) under each candidate configuration -- external levels
+ * per bulk task in {4, 8, 16} and 1 .. (occupancy limit) resident blocks per
+ * SM -- twice each, timed with events on `stream`, and keeps the fastest.
+ * Every configuration computes the same tables (the arithmetic is exact), and
+ * the call ends with one more solve under the chosen configuration, so the
+ * tables hold the solution on return.  It synchronises the stream, may
+ * reallocate the plan's workspace, and must not be called while capturing a
+ * graph; capture mcm_solve_batched afterwards. */
+dp_status mcm_plan_autotune(void *plan, const int32_t *p_all, const int64_t *p_off,
+                            const int64_t *tab_off, void *m_all, int16_t *s_all,
+                            int32_t *status_dev, void *stream);
+
+/* The configuration a plan currently uses (defaults until autotuned):
+ * levels per bulk task, and resident blocks per SM (0 = the occupancy limit). */
+dp_status mcm_plan_config(const void *plan, int32_t *levels_per_part, int32_t *blocks_per_sm);
+
 dp_status mcm_plan_destroy(void *plan);
 
 /* ------------------------------------------------------------------------- */

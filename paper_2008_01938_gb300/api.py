@@ -151,6 +151,19 @@ class McmPlan:
         check(lib.mcm_solve_batched(self._h, _ptr(p_all), _ptr(p_off), _ptr(tab_off), _ptr(m_all), _ptr(s_all),
                                     _ptr(status), _stream_ptr(stream)))
 
+    def autotune(self, p_all, p_off, tab_off, m_all, s_all, status=None, stream=None):
+        """mcm_plan_autotune: time the candidate configurations on these
+        buffers, keep the fastest (the tables hold the solution afterwards)."""
+        check(native.load().mcm_plan_autotune(self._h, _ptr(p_all), _ptr(p_off), _ptr(tab_off), _ptr(m_all),
+                                              _ptr(s_all), _ptr(status), _stream_ptr(stream)))
+        return self.config()
+
+    def config(self):
+        """(levels per bulk task, resident blocks per SM; 0 = occupancy limit)"""
+        lpp, bps = ctypes.c_int32(), ctypes.c_int32()
+        check(native.load().mcm_plan_config(self._h, ctypes.byref(lpp), ctypes.byref(bps)))
+        return int(lpp.value), int(bps.value)
+
     def destroy(self):
         if getattr(self, "_h", None):
             native.load().mcm_plan_destroy(self._h)

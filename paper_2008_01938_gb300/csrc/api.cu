@@ -130,7 +130,6 @@ McmStatic::~McmStatic() {
 }
 
 namespace {
-using dpk::kLevelsPerPart;
 using dpk::kMinBulkLevels;
 
 // Queue order: by the tile-diagonal at which a task becomes ready; within a
@@ -143,7 +142,9 @@ struct SortKey {
 };
 }  // namespace
 
-dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared_ptr<McmStatic>* out, bool upload) {
+dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared_ptr<McmStatic>* out, bool upload,
+                           int levels_per_part) {
+  const int kLevelsPerPart = levels_per_part > 0 ? levels_per_part : dpk::kLevelsPerPart;
   auto sp = std::make_shared<McmStatic>();
   sp->i64 = i64;
   sp->ns = ns;
@@ -264,7 +265,8 @@ McmLayout mcm_layout(const McmStatic& sp) {
 
 dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const int32_t* p_all,
                       const int64_t* p_off, const int64_t* tab_off, void* m_all, int16_t* s_all,
-                      int32_t* status, cudaStream_t st, long long limit_override, int32_t drop_task) {
+                      int32_t* status, cudaStream_t st, long long limit_override, int32_t drop_task,
+                      int blocks_per_sm) {
   DevState* ds = nullptr;
   dp_status rc = current_dev(&ds);
   if (rc != DP_OK) return rc;
@@ -300,7 +302,8 @@ dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const i
   a.s_all = s_all;
   if ((e = dpk::launch_mcm_prologue(a, sp.i64, st)) != cudaSuccess) return fail_cuda(e, "launch MCM prologue");
   const int c = sp.i64 ? 1 : 0;
-  const int grid = (int)std::max<int64_t>(2, std::min<int64_t>((int64_t)ds->sms * ds->occ[c], (int64_t)sp.tasks.size()));
+  const int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, ds->occ[c]) : ds->occ[c];
+  const int grid = (int)std::max<int64_t>(2, std::min<int64_t>((int64_t)ds->sms * bps, (int64_t)sp.tasks.size()));
   const bool prof = profiling();
   if (prof) profile_mark(0, st, false);
   if ((e = dpk::launch_mcm_main(a, sp.i64, std::max(grid, 1), st)) != cudaSuccess)
@@ -372,7 +375,12 @@ struct McmPlan {
   std::shared_ptr<McmStatic> sp;
   McmLayout L;
   void* ws = nullptr;
+  size_t ws_bytes = 0;
   int device = -1;
+  std::vector<int32_t> ns;
+  bool i64 = false;
+  int levels_per_part = dpk::kLevelsPerPart;  // queue granularity (chosen by mcm_plan_autotune)
+  int blocks_per_sm = 0;                      // resident blocks per SM, 0 = occupancy limit
 };
 
 struct SdpPlan {
@@ -522,7 +530,9 @@ dp_status mcm_plan_create(int32_t batch, const int32_t* n_host, dp_cost ct, void
   dp_status rc = current_dev(&ds);
   if (rc != DP_OK) return rc;
   auto* pl = new McmPlan();
-  rc = mcm_build_static(std::vector<int32_t>(n_host, n_host + batch), ct == DP_COST_I64, &pl->sp);
+  pl->ns.assign(n_host, n_host + batch);
+  pl->i64 = ct == DP_COST_I64;
+  rc = mcm_build_static(pl->ns, pl->i64, &pl->sp);
   if (rc != DP_OK) {
     delete pl;
     return rc;
@@ -534,6 +544,7 @@ dp_status mcm_plan_create(int32_t batch, const int32_t* n_host, dp_cost ct, void
     delete pl;
     return fail_cuda(e, "mcm_plan_create: workspace");
   }
+  pl->ws_bytes = pl->L.total;
   *plan = pl;
   return DP_OK;
 }
@@ -544,7 +555,88 @@ dp_status mcm_solve_batched(void* plan, const int32_t* p_all, const int64_t* p_o
   if (!pl || !p_all || !p_off || !tab_off || !m_all || !s_all)
     return fail(DP_EINVAL, "mcm_solve_batched: NULL argument");
   return mcm_enqueue(*pl->sp, pl->L, pl->ws, p_all, p_off, tab_off, m_all, s_all, status_dev,
-                     static_cast<cudaStream_t>(stream));
+                     static_cast<cudaStream_t>(stream), 0, -1, pl->blocks_per_sm);
+}
+
+dp_status mcm_plan_autotune(void* plan, const int32_t* p_all, const int64_t* p_off, const int64_t* tab_off,
+                            void* m_all, int16_t* s_all, int32_t* status_dev, void* stream) {
+  auto* pl = static_cast<McmPlan*>(plan);
+  if (!pl || !p_all || !p_off || !tab_off || !m_all || !s_all)
+    return fail(DP_EINVAL, "mcm_plan_autotune: NULL argument");
+  DevState* ds = nullptr;
+  dp_status rc = current_dev(&ds);
+  if (rc != DP_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int occ = ds->occ[pl->i64 ? 1 : 0];
+  cudaEvent_t e0, e1;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
+    return fail_cuda(e, "mcm_plan_autotune: events");
+  float best_ms = -1.0f;
+  int best_lpp = pl->levels_per_part, best_bps = pl->blocks_per_sm;
+  std::shared_ptr<McmStatic> best_sp = pl->sp;
+  for (int lpp : {4, 8, 16}) {
+    std::shared_ptr<McmStatic> sp;
+    if (lpp == pl->levels_per_part) {
+      sp = pl->sp;
+    } else if ((rc = mcm_build_static(pl->ns, pl->i64, &sp, true, lpp)) != DP_OK) {
+      break;
+    }
+    const McmLayout L = mcm_layout(*sp);
+    if (L.total > pl->ws_bytes) {  // a finer queue needs more partial-minimum slots
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        rc = fail_cuda(e, "mcm_plan_autotune: sync");
+        break;
+      }
+      cudaFree(pl->ws);
+      pl->ws = nullptr;
+      pl->ws_bytes = 0;
+      if ((e = cudaMalloc(&pl->ws, L.total)) != cudaSuccess) {
+        rc = fail_cuda(e, "mcm_plan_autotune: workspace");
+        break;
+      }
+      pl->ws_bytes = L.total;
+    }
+    for (int bps = 1; bps <= occ; ++bps) {
+      float t = 0.0f, tmin = -1.0f;
+      for (int rep = 0; rep < 2 && rc == DP_OK; ++rep) {
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) rc = fail_cuda(e, "mcm_plan_autotune: event");
+        if (rc == DP_OK)
+          rc = mcm_enqueue(*sp, L, pl->ws, p_all, p_off, tab_off, m_all, s_all, status_dev, st, 0, -1, bps);
+        if (rc == DP_OK && (e = cudaEventRecord(e1, st)) != cudaSuccess) rc = fail_cuda(e, "mcm_plan_autotune: event");
+        if (rc == DP_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = fail_cuda(e, "mcm_plan_autotune: sync");
+        if (rc == DP_OK && (e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess)
+          rc = fail_cuda(e, "mcm_plan_autotune: timing");
+        if (rc == DP_OK && (tmin < 0.0f || t < tmin)) tmin = t;
+      }
+      if (rc != DP_OK) break;
+      if (best_ms < 0.0f || tmin < best_ms) {
+        best_ms = tmin;
+        best_lpp = lpp;
+        best_bps = bps;
+        best_sp = sp;
+      }
+    }
+    if (rc != DP_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DP_OK) return rc;
+  pl->sp = best_sp;
+  pl->L = mcm_layout(*best_sp);
+  pl->levels_per_part = best_lpp;
+  pl->blocks_per_sm = best_bps;
+  // leave the tables solved with the chosen configuration
+  return mcm_enqueue(*pl->sp, pl->L, pl->ws, p_all, p_off, tab_off, m_all, s_all, status_dev, st, 0, -1,
+                     pl->blocks_per_sm);
+}
+
+dp_status mcm_plan_config(const void* plan, int32_t* levels_per_part, int32_t* blocks_per_sm) {
+  const auto* pl = static_cast<const McmPlan*>(plan);
+  if (!pl) return fail(DP_EINVAL, "mcm_plan_config: NULL plan");
+  if (levels_per_part) *levels_per_part = pl->levels_per_part;
+  if (blocks_per_sm) *blocks_per_sm = pl->blocks_per_sm;
+  return DP_OK;
 }
 
 dp_status mcm_plan_destroy(void* plan) {

@@ -62,14 +62,15 @@ struct McmLayout {
 
 // Builds the work queue on the host; with upload=true also copies the queue,
 // slot table and chain records to fresh device memory owned by the result.
+// levels_per_part: external levels per bulk task (0 = the default).
 dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared_ptr<McmStatic>* out,
-                           bool upload = true);
+                           bool upload = true, int levels_per_part = 0);
 McmLayout mcm_layout(const McmStatic& sp);
 // Enqueues memsets + prologue + main kernel for a static plan on `ws`.
 dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const int32_t* p_all,
                       const int64_t* p_off, const int64_t* tab_off, void* m_all, int16_t* s_all,
                       int32_t* status, cudaStream_t st, long long limit_override = 0,
-                      int32_t drop_task = -1);
+                      int32_t drop_task = -1, int blocks_per_sm = 0);
 
 // ---------------------------------------------------------------------------
 // S-DP

@@ -199,6 +199,44 @@ def test_batched_parity(dp, cost):
     plan.destroy()
 
 
+@pytest.mark.parametrize("cost", ["i64", "i32"])
+def test_batched_autotune(dp, cost):
+    """The autotuner picks one of its candidate configurations, leaves the
+    tables solved, and later solves under the chosen configuration (also
+    captured in a graph) agree with the oracle."""
+    import torch
+    hi = 1000 if cost == "i64" else 32
+    b = inputs.mcm_batch(count=80, nlo=8, nhi=400, dlo=1, dhi=hi, seed=23)
+    plan = dp.McmPlan(b.ns, cost=cost)
+    assert plan.config() == (8, 0)                    # defaults before tuning
+    t = _batch_tensors(b, cost)
+    lpp, bps = plan.autotune(*t)
+    dp.sync_status()
+    assert lpp in (4, 8, 16) and bps >= 1
+    assert plan.config() == (lpp, bps)
+
+    def check_all():
+        m_all, s_all = t[3].cpu().numpy(), t[4].cpu().numpy()
+        for i in range(b.ns.size):
+            n, o = int(b.ns[i]), int(b.tab_off[i])
+            om, os_ = oracle.mcm(b.dims(i))
+            assert np.array_equal(m_all[o:o + n * n].reshape(n, n).astype(np.int64), om), i
+            assert np.array_equal(s_all[o:o + n * n].reshape(n, n), os_), i
+
+    check_all()                                       # left solved by the tuner
+    t[3].fill_(-1)
+    t[4].fill_(-1)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.solve(*t, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    dp.sync_status()
+    check_all()
+    plan.destroy()
+
+
 def test_batched_graph_capture_replay(dp):
     import torch
     b = inputs.mcm_batch(count=60, nlo=8, nhi=200, seed=22)
