@@ -125,6 +125,23 @@ dp_status mcm_solve(const int32_t *p, int32_t n, dp_cost ct, void *m, int16_t *s
 dp_status mcm_solve_noalloc(const int32_t *p, int32_t n, int32_t *m, int16_t *s, int32_t *status_dev,
                             void *stream);
 
+/* The optimal parenthesisation encoded by a split table (the textbook's
+ * PRINT-OPTIMAL-PARENS, which the paper's MCM recurrence follows), on the
+ * device.
+ *   s       device int16[n*n] as written by mcm_solve (split of (i, j) at
+ *           s[i*n + j]).
+ *   steps   device int32[3*(n-1)], filled with the n-1 products in post-order:
+ *           entry t is (i, k, j) = multiply the product of matrices i..k by
+ *           that of k+1..j; both operands are single matrices or results of
+ *           earlier entries, and the last entry is (0, k, n-1).
+ * Nothing is written for n = 1 (steps may then be NULL).  The tree is
+ * expanded one level per pass of one block, so the time grows with the tree's
+ * depth (at most n-1 levels).  A split outside [i, j) is reported as
+ * DP_EINVAL in *status_dev (NULL: the library's status word, read by
+ * dp_sync_status).  A small stream-ordered scratch allocation holds the
+ * levels; NULL s or steps (n > 1) or n outside [1, 32767] return DP_EINVAL. */
+dp_status mcm_traceback(const int16_t *s, int32_t n, int32_t *steps, int32_t *status_dev, void *stream);
+
 /* Same computation with HOST buffers: copies p (n+1 int32) to the device,
  * solves, copies m and s back, and waits for completion.  Host buffers may be
  * pageable or pinned (pinned is faster). */

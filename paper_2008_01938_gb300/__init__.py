@@ -15,6 +15,7 @@ from .api import (  # noqa: F401
     Server,
     mcm_solve,
     mcm_solve_host,
+    mcm_traceback,
     sdp_solve,
     sdp_solve_host,
     sync_status,

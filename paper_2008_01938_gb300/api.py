@@ -104,6 +104,24 @@ def mcm_solve_noalloc(p, m, s, status, stream=None):
     return m, s
 
 
+def mcm_traceback(s, steps=None, status=None, stream=None):
+    """Optimal parenthesisation from a split table (CUDA int16 n x n, as
+    written by mcm_solve): int32 (n-1, 3) products (i, k, j) in post-order."""
+    torch = _torch()
+    lib = native.load()
+    _need(s, torch.int16, "s")
+    n = int(s.shape[0]) if s.dim() == 2 else int(round(s.numel() ** 0.5))
+    if n * n != s.numel():
+        raise ValueError("s must hold n*n entries")
+    if steps is None:
+        steps = torch.empty((max(n - 1, 0), 3), dtype=torch.int32, device=s.device)
+    _need(steps, torch.int32, "steps", 3 * max(n - 1, 0))
+    if status is not None:
+        _need(status, torch.int32, "status", 1)
+    check(lib.mcm_traceback(_ptr(s), n, _ptr(steps), _ptr(status), _stream_ptr(stream)))
+    return steps
+
+
 def mcm_solve_host(p, cost="i32", m=None, s=None, stream=None):
     """Host-buffer form: numpy (or pinned torch CPU) dims in, tables out."""
     lib = native.load()
