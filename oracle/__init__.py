@@ -12,6 +12,8 @@ through ctypes.
                               (problem from Cormen et al., cited there)
   mcm_cell(p, i, j)        -> (m[i][j], s[i][j]) by solving the sub-chain
                               A_i..A_j alone (the sub-problem is self-contained)
+  interval(p, w)           -> (m int64[n, n], s int16[n, n])   Eq. (2) with
+                              f(l, r) = l + r + p[i] p[k+1] p[j+1] + w[i][j]
   sdp(preset, n, a, op)    -> uint32[n]                        Definition 1, Fig. 1
   diag_major_index(n,r,c)  -> the 1-based position of CLRS cell (r, c) in the
                               paper's linearised table (Section IV-B)
@@ -53,6 +55,9 @@ def _load():
             lib = ctypes.CDLL(_LIB)
             lib.dp_oracle_mcm.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
             lib.dp_oracle_mcm.restype = ctypes.c_int
+            lib.dp_oracle_interval.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_void_p]
+            lib.dp_oracle_interval.restype = ctypes.c_int
             lib.dp_oracle_sdp.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
             lib.dp_oracle_sdp.restype = ctypes.c_int
             _lib = lib
@@ -82,6 +87,34 @@ def mcm_cell(p, i: int, j: int) -> tuple[int, int]:
     A_i..A_j only (dims p[i..j+1])."""
     sub = np.asarray(p, dtype=np.int32)[i:j + 2]
     m, s = mcm(sub)
+    kk = int(s[0, j - i])
+    return int(m[0, j - i]), (kk + i if kk >= 0 else -1)
+
+
+def interval(p, w) -> tuple[np.ndarray, np.ndarray]:
+    """Interval-DP tables for rank-1 factors p[0..n] (>= 0) and the per-cell
+    weight w (n x n, entries with i < j read, >= 0): m (int64) and s (int16),
+    m = 0 and s = -1 on and below the diagonal, ties to the smallest k."""
+    lib = _load()
+    p = np.ascontiguousarray(np.asarray(p, dtype=np.int32))
+    n = int(p.size) - 1
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.int64))
+    if w.shape != (n, n):
+        raise ValueError(f"w must be {n} x {n}, got {w.shape}")
+    m = np.empty((max(n, 0), max(n, 0)), dtype=np.int64)
+    s = np.empty((max(n, 0), max(n, 0)), dtype=np.int16)
+    rc = lib.dp_oracle_interval(p.ctypes.data, w.ctypes.data, n, m.ctypes.data, s.ctypes.data)
+    if rc != 0:
+        raise OracleError(f"dp_oracle_interval failed with status {rc}")
+    return m, s
+
+
+def interval_cell(p, w, i: int, j: int) -> tuple[int, int]:
+    """m[i][j] and s[i][j] of the interval DP, from the sub-problem on
+    i..j alone (p[i..j+1] and the block w[i..j, i..j])."""
+    sub_p = np.asarray(p, dtype=np.int32)[i:j + 2]
+    sub_w = np.asarray(w, dtype=np.int64)[i:j + 1, i:j + 1]
+    m, s = interval(sub_p, sub_w)
     kk = int(s[0, j - i])
     return int(m[0, j - i]), (kk + i if kk >= 0 else -1)
 

@@ -14,6 +14,10 @@
  *                     textbook recurrence is written out here).
  *   dp_oracle_sdp  -- simplified DP problem, Definition 1 / Eq. (1), filled by
  *                     the sequential algorithm of Fig. 1.
+ *   dp_oracle_interval -- the triangular-table DP of Section IV with a more
+ *                     general combining function f of Eq. (2): the MCM
+ *                     weight plus a per-cell weight w[i][j] (the paper
+ *                     presents MCM as one instance of the general technique).
  *
  * Readings where the paper is silent (each is also listed in the design doc):
  *   - indices are 0-based: chain A_0..A_{n-1}, A_i is p[i] x p[i+1];
@@ -64,6 +68,57 @@ int dp_oracle_mcm(const int32_t *p, int32_t n, int64_t *m, int16_t *s)
                 if (left > INT64_MAX - right || left + right > INT64_MAX - w)
                     return ORACLE_EOVERFLOW;
                 const int64_t cand = left + right + w;
+                if (best_k < 0 || cand < best) {
+                    best = cand;
+                    best_k = k;
+                }
+            }
+            m[(int64_t)i * n + j] = best;
+            s[(int64_t)i * n + j] = (int16_t)best_k;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/*
+ * Interval DP with a user weight.  For i < j:
+ *     m[i][j] = min over i <= k < j of
+ *                 m[i][k] + m[k+1][j] + p[i]*p[k+1]*p[j+1] + w[i][j]
+ *     s[i][j] = the smallest k attaining that minimum,
+ * i.e. Eq. (2) with f(l, r) = l + r + p[i]*p[k+1]*p[j+1] + w[i][j].  With w = 0
+ * this is dp_oracle_mcm; with p = 0 it is the split form of Knuth's optimal
+ * binary search tree and of optimal merging.  p[0..n] >= 0; w is n*n
+ * row-major and only its entries with i < j are read (each >= 0).  Same fill
+ * order, tie rule and overflow checks as dp_oracle_mcm.
+ */
+int dp_oracle_interval(const int32_t *p, const int64_t *w, int32_t n, int64_t *m, int16_t *s)
+{
+    if (n < 1 || n > 32767) return ORACLE_EINVAL;
+    for (int32_t t = 0; t <= n; ++t)
+        if (p[t] < 0) return ORACLE_EINVAL;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = i + 1; j < n; ++j)
+            if (w[(int64_t)i * n + j] < 0) return ORACLE_EINVAL;
+    for (int64_t t = 0; t < (int64_t)n * n; ++t) {
+        m[t] = 0;
+        s[t] = -1;
+    }
+    for (int32_t d = 1; d < n; ++d) {
+        for (int32_t i = 0; i + d < n; ++i) {
+            const int32_t j = i + d;
+            const int64_t wij = w[(int64_t)i * n + j];
+            int64_t best = 0;
+            int32_t best_k = -1;
+            for (int32_t k = i; k < j; ++k) {
+                const int64_t a = p[i], b = p[k + 1], c = p[j + 1];
+                if (c != 0 && a * b > INT64_MAX / c) return ORACLE_EOVERFLOW;
+                const int64_t r1 = a * b * c;
+                const int64_t left = m[(int64_t)i * n + k];
+                const int64_t right = m[(int64_t)(k + 1) * n + j];
+                if (left > INT64_MAX - right || left + right > INT64_MAX - r1 ||
+                    left + right + r1 > INT64_MAX - wij)
+                    return ORACLE_EOVERFLOW;
+                const int64_t cand = left + right + r1 + wij;
                 if (best_k < 0 || cand < best) {
                     best = cand;
                     best_k = k;
