@@ -99,6 +99,28 @@ dp_status dp_profile_end(double *mcm_ms, int64_t *mcm_launches, double *sdp_ms, 
 dp_status mcm_solve(const int32_t *p, int32_t n, dp_cost ct, void *m, int16_t *s,
                     int32_t *status_dev, void *stream);
 
+/* Interval DP with a user weight: the triangular-table DP of Section IV with
+ * Eq. (2)'s f taken more generally (the paper presents MCM as one instance of
+ * its technique).  For i < j
+ *     m[i][j] = min_{i <= k < j} m[i][k] + m[k+1][j] + p[i]*p[k+1]*p[j+1] + w[i][j]
+ * and s[i][j] = the smallest minimising k; m = 0 and s = -1 on and below the
+ * diagonal.  w = 0 gives mcm_solve; p = 0 gives the split form of Knuth's
+ * optimal binary search tree (cells = gaps 0..n-1 between keys, w[i][j] = the
+ * weight of keys i+1..j and gaps i..j, root key = s + 1) and optimal merging.
+ *   p       device int32[n+1], 0 <= p[t] < 65536 (DP_EINVAL / DP_EOVERFLOW in
+ *           *status_dev otherwise).
+ *   w       device int32[n*n], row-major (ld = n), the same layout as m;
+ *           only entries with i < j are read, each >= 0 (DP_EINVAL in
+ *           *status_dev otherwise).
+ *   ct      DP_COST_I32 only (m int32, (n-1)*(max(p)^3 + max(w)) < 2^31,
+ *           DP_EOVERFLOW in *status_dev otherwise); DP_COST_I64 returns
+ *           DP_EINVAL.
+ *   n, m, s, status_dev, stream: as for mcm_solve.
+ * A device pass over w (one extra launch) finds max(w) before the solve.
+ * NULL p, w, m or s return DP_EINVAL. */
+dp_status interval_dp_solve(const int32_t *p, const void *w, int32_t n, dp_cost ct, void *m, int16_t *s,
+                            int32_t *status_dev, void *stream);
+
 /* mcm_solve for int32 costs that allocates no memory.  The paper has no
  * counterpart: it exists for callers that cannot allocate when they solve --
  * a process whose free device memory belongs to its own allocator (where a

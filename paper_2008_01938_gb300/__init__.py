@@ -13,6 +13,7 @@ from .api import (  # noqa: F401
     McmPlan,
     SdpPlan,
     Server,
+    interval_dp_solve,
     mcm_solve,
     mcm_solve_host,
     mcm_traceback,

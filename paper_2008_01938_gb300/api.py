@@ -89,6 +89,31 @@ def mcm_solve(p, cost="i32", m=None, s=None, status=None, stream=None):
     return m, s
 
 
+def interval_dp_solve(p, w, cost="i32", m=None, s=None, status=None, stream=None):
+    """Interval DP with a user weight: Eq. (2) with
+    f(l, r) = l + r + p[i] p[k+1] p[j+1] + w[i][j].  ``p`` CUDA int32 (n+1),
+    entries >= 0 (zeros drop the rank-1 term); ``w`` CUDA int32 (n, n), only
+    entries with i < j read, each >= 0.  Int32 costs only (cost="i64" is
+    refused by the library).  Returns (m, s) like mcm_solve."""
+    torch = _torch()
+    lib = native.load()
+    ct = _cost(cost)
+    _need(p, torch.int32, "p")
+    n = p.numel() - 1
+    mdt = torch.int32 if ct == native.DP_COST_I32 else torch.int64
+    _need(w, mdt, "w", n * n)
+    if m is None:
+        m = torch.empty((n, n), dtype=mdt, device=p.device)
+    if s is None:
+        s = torch.empty((n, n), dtype=torch.int16, device=p.device)
+    _need(m, mdt, "m", n * n)
+    _need(s, torch.int16, "s", n * n)
+    if status is not None:
+        _need(status, torch.int32, "status", 1)
+    check(lib.interval_dp_solve(_ptr(p), _ptr(w), n, ct, _ptr(m), _ptr(s), _ptr(status), _stream_ptr(stream)))
+    return m, s
+
+
 def mcm_solve_noalloc(p, m, s, status, stream=None):
     """mcm_solve for int32 costs through the entry point that allocates
     nothing: the caller passes every buffer (p int32 n+1, m int32 and s int16

@@ -266,7 +266,7 @@ McmLayout mcm_layout(const McmStatic& sp) {
 dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const int32_t* p_all,
                       const int64_t* p_off, const int64_t* tab_off, void* m_all, int16_t* s_all,
                       int32_t* status, cudaStream_t st, long long limit_override, int32_t drop_task,
-                      int blocks_per_sm) {
+                      int blocks_per_sm, const void* w_all) {
   DevState* ds = nullptr;
   dp_status rc = current_dev(&ds);
   if (rc != DP_OK) return rc;
@@ -300,6 +300,9 @@ dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const i
   a.tab_off = tab_off;
   a.m_all = m_all;
   a.s_all = s_all;
+  a.w_all = w_all;
+  if (w_all && (e = dpk::launch_mcm_weight_max(a, sp.i64, ds->sms, st)) != cudaSuccess)
+    return fail_cuda(e, "launch weight pass");
   if ((e = dpk::launch_mcm_prologue(a, sp.i64, st)) != cudaSuccess) return fail_cuda(e, "launch MCM prologue");
   const int c = sp.i64 ? 1 : 0;
   const int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, ds->occ[c]) : ds->occ[c];
@@ -394,22 +397,24 @@ struct SdpPlan {
 };
 
 dp_status mcm_solve_impl(const int32_t* p, int32_t n, dp_cost ct, void* m, int16_t* s, int32_t* status_dev,
-                         cudaStream_t st, long long limit_override, int32_t drop_task) {
-  if (!p || !m || !s) return fail(DP_EINVAL, "mcm_solve: NULL pointer argument");
-  if (n < 1 || n > 32767) return fail(DP_EINVAL, "mcm_solve: n = %d outside [1, 32767]", n);
-  if (ct != DP_COST_I32 && ct != DP_COST_I64) return fail(DP_EINVAL, "mcm_solve: unknown cost type %d", (int)ct);
+                         cudaStream_t st, long long limit_override, int32_t drop_task, const void* w = nullptr) {
+  const char* who = w ? "interval_dp_solve" : "mcm_solve";
+  if (!p || !m || !s) return fail(DP_EINVAL, "%s: NULL pointer argument", who);
+  if (n < 1 || n > 32767) return fail(DP_EINVAL, "%s: n = %d outside [1, 32767]", who, n);
+  if (ct != DP_COST_I32 && ct != DP_COST_I64) return fail(DP_EINVAL, "%s: unknown cost type %d", who, (int)ct);
   const bool i64 = ct == DP_COST_I64;
+  if (w && i64) return fail(DP_EINVAL, "interval_dp_solve: only DP_COST_I32 is available");
   std::shared_ptr<McmStatic> sp;
   dp_status rc = single_plan(n, i64, &sp);
   if (rc != DP_OK) return rc;
   const McmLayout L = mcm_layout(*sp);
   void* ws = nullptr;
   cudaError_t e = cudaMallocAsync(&ws, L.total, st);
-  if (e != cudaSuccess) return fail_cuda(e, "mcm_solve: workspace allocation");
-  rc = mcm_enqueue(*sp, L, ws, p, nullptr, nullptr, m, s, status_dev, st, limit_override, drop_task);
+  if (e != cudaSuccess) return fail_cuda(e, w ? "interval_dp_solve: workspace allocation" : "mcm_solve: workspace allocation");
+  rc = mcm_enqueue(*sp, L, ws, p, nullptr, nullptr, m, s, status_dev, st, limit_override, drop_task, 0, w);
   e = cudaFreeAsync(ws, st);
   if (rc != DP_OK) return rc;
-  if (e != cudaSuccess) return fail_cuda(e, "mcm_solve: workspace release");
+  if (e != cudaSuccess) return fail_cuda(e, w ? "interval_dp_solve: workspace release" : "mcm_solve: workspace release");
   return DP_OK;
 }
 }  // namespace
@@ -482,6 +487,12 @@ dp_status dp_sync_status(void* stream, int32_t* status_dev) {
 dp_status mcm_solve(const int32_t* p, int32_t n, dp_cost ct, void* m, int16_t* s, int32_t* status_dev,
                     void* stream) {
   return mcm_solve_impl(p, n, ct, m, s, status_dev, static_cast<cudaStream_t>(stream), 0, -1);
+}
+
+dp_status interval_dp_solve(const int32_t* p, const void* w, int32_t n, dp_cost ct, void* m, int16_t* s,
+                            int32_t* status_dev, void* stream) {
+  if (!w) return fail(DP_EINVAL, "interval_dp_solve: NULL pointer argument");
+  return mcm_solve_impl(p, n, ct, m, s, status_dev, static_cast<cudaStream_t>(stream), 0, -1, w);
 }
 
 // Fault-injection hook for tests: like mcm_solve, but queue entry `drop_task`

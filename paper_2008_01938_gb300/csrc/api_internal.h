@@ -67,10 +67,12 @@ dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared
                            bool upload = true, int levels_per_part = 0);
 McmLayout mcm_layout(const McmStatic& sp);
 // Enqueues memsets + prologue + main kernel for a static plan on `ws`.
+// w_all != nullptr: the interval DP with per-cell weights laid out like m_all
+// (a weight pass is enqueued before the prologue).
 dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const int32_t* p_all,
                       const int64_t* p_off, const int64_t* tab_off, void* m_all, int16_t* s_all,
                       int32_t* status, cudaStream_t st, long long limit_override = 0,
-                      int32_t drop_task = -1, int blocks_per_sm = 0);
+                      int32_t drop_task = -1, int blocks_per_sm = 0, const void* w_all = nullptr);
 
 // ---------------------------------------------------------------------------
 // S-DP

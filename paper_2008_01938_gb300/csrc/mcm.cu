@@ -264,7 +264,7 @@ __device__ __forceinline__ void for_each_segment(const McmTask& t, F&& body) {
   }
 }
 
-template <bool I64>
+template <bool I64, bool W>
 __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(const McmLaunchArgs a) {
   using E = typename Cost<I64>::E;
   constexpr int KB = Cost<I64>::KB;
@@ -477,6 +477,15 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
         // ------------------ in-tile wavefront (finisher) ------------------
         // layout: warp w owns rows 4w..4w+3, lane = column
         const int w = warp;
+        // interval DP: the weights of the thread's 4 cells, loaded while the copies land
+        E wt[4] = {0, 0, 0, 0};
+        if constexpr (W) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int64_t i = IT + 4 * w + r, j = JT + lane;
+            if (i < j && j < inst.n) wt[r] = static_cast<const E*>(inst.w)[i * inst.n + j];
+          }
+        }
         const uint32_t fpar = fin_cnt & 1u;
         const bool fin_ok = mbar_wait(bar_fin, fpar, limit);
         if (!fin_ok) set_status(status, DP_ETIMEOUT);
@@ -537,8 +546,8 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
             const int c0 = lane - 4 * w - 1;   // at step e the lane's cell in row 4w + c0 - e becomes final
             bar_compute();
             if (w == 7 && lane == 0) {  // cell (31, 0), the only cell of diagonal -31
-              Xr[T - 1] = m[3];
-              Xc[0] = m[3];
+              Xr[T - 1] = m[3] + wt[3];
+              Xc[0] = m[3] + wt[3];
             }
             // Operands of the first step.  Window slot (u & 3) holds L[u][lane]
             // and p[JT + u + 1] for u = 4w + e .. 4w + e + 3; with e = 1 mod 4
@@ -575,7 +584,8 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
                     // the lane's cell on diagonal e + 1 is final now
                     const int rr = c0 - e;
                     const bool own = (unsigned)rr <= 3u;
-                    const E v = sel4(rr, m[0], m[1], m[2], m[3]);
+                    E v = sel4(rr, m[0], m[1], m[2], m[3]);
+                    if constexpr (W) v += sel4(rr, wt[0], wt[1], wt[2], wt[3]);
                     sts_if(own, sXr + (uint32_t)(((dI + 1) * T + 4 * w + rr) * (int)sizeof(E)), v);
                     sts_if(own, sXc + (uint32_t)(((dI + 1) * T + lane) * (int)sizeof(E)), v);
                     // operands of step e + 1 (independent of the tile values)
@@ -658,7 +668,8 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
               const int64_t i = IT + li, j = JT + lane;
               if (i >= nn || j >= nn) continue;
               // (register arrays are read through sel4: a runtime index would move them to local memory)
-              const E v = sel4(r, vals[0], vals[1], vals[2], vals[3]);
+              E v = sel4(r, vals[0], vals[1], vals[2], vals[3]);  // the minimum, less the cell's own weight
+              if constexpr (W) v -= sel4(r, wt[0], wt[1], wt[2], wt[3]);
               const E wr = sel4(r, wv[0], wv[1], wv[2], wv[3]);
               int k = -1;
               for (int t = li; t <= T - 2; ++t) {
@@ -691,7 +702,7 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
 #pragma unroll
               for (int r = 0; r < 4; ++r) {
                 const int li = 4 * w + r;
-                if (lane - li == e) Xv[li * T + lane] = e == 0 ? (E)0 : (E)(cb[r] >> KB);
+                if (lane - li == e) Xv[li * T + lane] = e == 0 ? (E)0 : (E)(cb[r] >> KB) + wt[r];
               }
               bar_compute();
 #pragma unroll
@@ -721,7 +732,7 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
             const int li = 4 * w + r;
             const int64_t i = IT + li, j = JT + lane;
             const bool upper = D >= 1 || li < lane;
-            const E v = upper ? (E)(cb[r] >> KB) : (E)0;
+            const E v = upper ? (E)(cb[r] >> KB) + wt[r] : (E)0;
             const int kk = upper ? (int)(cb[r] & kmask) : -1;
             vals[r] = v;
             if (i < nn && j < nn) {
@@ -785,9 +796,43 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
   }
 }
 
+// Interval DP, before the prologue: the largest weight above the diagonal of
+// each chain (blockIdx.y), merged into McmInstDev::wmax; a negative weight
+// there is DP_EINVAL.  Entries on and below the diagonal are not read.
+// Weights are int32 (the cost type the interval DP is built for).
+__global__ void __launch_bounds__(256) mcm_weight_max_kernel(const McmLaunchArgs a) {
+  using SW = int32_t;
+  __shared__ unsigned long long s_max[8];
+  const int b = blockIdx.y;
+  McmInstDev* inst = a.insts + b;
+  const int n = inst->n;
+  const SW* w = static_cast<const SW*>(a.w_all) + (a.tab_off ? a.tab_off[b] : 0);
+  unsigned long long mx = 0;
+  bool neg = false;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const SW* row = w + (int64_t)i * n;
+    for (int j = i + 1 + (int)threadIdx.x; j < n; j += blockDim.x) {
+      const SW v = row[j];
+      neg |= v < 0;
+      mx = v > 0 && (unsigned long long)v > mx ? (unsigned long long)v : mx;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = x > mx ? x : mx;
+  }
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+  neg = __syncthreads_or(neg);
+  if (threadIdx.x == 0) {
+    for (int x = 1; x < (int)(blockDim.x >> 5); ++x) mx = s_max[x] > mx ? s_max[x] : mx;
+    if (neg) set_status(a.status, DP_EINVAL);
+    if (mx > 0) atomicMax(&inst->wmax, mx);
+  }
+}
+
 // One block per chain: validates dims, derives the cost bound and the packing
 // shift, writes the padded / shifted dim arrays and the chain's pointers.
-template <bool I64>
+template <bool I64, bool W>
 __global__ void __launch_bounds__(256) mcm_prologue_kernel(const McmLaunchArgs a) {
   __shared__ int32_t s_max[8], s_min[8];
   __shared__ int32_t s_shift;
@@ -816,13 +861,16 @@ __global__ void __launch_bounds__(256) mcm_prologue_kernel(const McmLaunchArgs a
       mn = min(mn, s_min[w]);
     }
     int shift = -1;
-    if (mn < 1) {
+    // interval DP: dims may be 0 (no rank-1 term); the weight adds at most
+    // wmax per product, and n - 1 products make up a cell
+    const unsigned long long wm = W ? inst->wmax : 0ull;
+    if (mn < (W ? 0 : 1)) {
       set_status(a.status, DP_EINVAL);
-    } else if (mx >= 65536) {
+    } else if (mx >= 65536 || wm >= (1ull << 47)) {
       set_status(a.status, DP_EOVERFLOW);
     } else {
-      const unsigned long long m3 = (unsigned long long)mx * mx * mx;      // < 2^48
-      const unsigned long long bound = (unsigned long long)(n - 1) * m3;   // < 2^63
+      const unsigned long long m3 = (unsigned long long)mx * mx * mx;         // < 2^48
+      const unsigned long long bound = (unsigned long long)(n - 1) * (m3 + wm);  // < 2^64
       if (I64) {
         if (bound >= (1ull << 47)) set_status(a.status, DP_EOVERFLOW);
         else shift = 16;
@@ -841,6 +889,7 @@ __global__ void __launch_bounds__(256) mcm_prologue_kernel(const McmLaunchArgs a
     const int64_t to = a.tab_off ? a.tab_off[b] : 0;
     inst->m = static_cast<uint8_t*>(a.m_all) + to * (I64 ? 8 : 4);
     inst->s = a.s_all + to;
+    if (W) inst->w = static_cast<const uint8_t*>(a.w_all) + to * (I64 ? 8 : 4);
   }
   __syncthreads();
   const int shift = s_shift;
@@ -857,18 +906,24 @@ __global__ void __launch_bounds__(256) mcm_prologue_kernel(const McmLaunchArgs a
 size_t mcm_smem_bytes(bool i64) { return i64 ? Smem<true>::TOTAL : Smem<false>::TOTAL; }
 
 cudaError_t mcm_configure(bool i64) {
+  cudaError_t e;
   if (i64)
-    return cudaFuncSetAttribute(mcm_main_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(mcm_main_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Smem<true>::TOTAL);
-  return cudaFuncSetAttribute(mcm_main_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(mcm_main_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Smem<false>::TOTAL)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(mcm_main_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Smem<false>::TOTAL);
 }
 
+// Both instances of a cost type have the same launch bounds and shared
+// memory, hence the same occupancy.
 cudaError_t mcm_occupancy(bool i64, int* blocks_per_sm) {
   if (i64)
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mcm_main_kernel<true>, kMcmThreads,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mcm_main_kernel<true, false>, kMcmThreads,
                                                          Smem<true>::TOTAL);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mcm_main_kernel<false>, kMcmThreads,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, mcm_main_kernel<false, false>, kMcmThreads,
                                                        Smem<false>::TOTAL);
 }
 
@@ -876,28 +931,47 @@ cudaError_t mcm_preload(bool i64) {
   cudaFuncAttributes fa;
   cudaError_t e;
   if (i64) {
-    if ((e = cudaFuncGetAttributes(&fa, mcm_prologue_kernel<true>)) != cudaSuccess) return e;
-    return cudaFuncGetAttributes(&fa, mcm_main_kernel<true>);
+    if ((e = cudaFuncGetAttributes(&fa, mcm_prologue_kernel<true, false>)) != cudaSuccess) return e;
+    return cudaFuncGetAttributes(&fa, mcm_main_kernel<true, false>);
   }
-  if ((e = cudaFuncGetAttributes(&fa, mcm_prologue_kernel<false>)) != cudaSuccess) return e;
-  return cudaFuncGetAttributes(&fa, mcm_main_kernel<false>);
+  if ((e = cudaFuncGetAttributes(&fa, mcm_prologue_kernel<false, false>)) != cudaSuccess) return e;
+  return cudaFuncGetAttributes(&fa, mcm_main_kernel<false, false>);
+}
+
+// The interval DP is built for int32 costs only (see launch_mcm_weight_max
+// in mcm_kernels.cuh): with int64 costs and weights these return
+// cudaErrorNotSupported and launch nothing.
+cudaError_t launch_mcm_weight_max(const McmLaunchArgs& a, bool i64, int sms, cudaStream_t st) {
+  if (a.ninst <= 0 || !a.w_all) return cudaSuccess;
+  if (i64) return cudaErrorNotSupported;
+  const dim3 grid((unsigned)(sms > 0 ? 4 * sms : 256), (unsigned)a.ninst);
+  mcm_weight_max_kernel<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_mcm_prologue(const McmLaunchArgs& a, bool i64, cudaStream_t st) {
   if (a.ninst <= 0) return cudaSuccess;
-  if (i64)
-    mcm_prologue_kernel<true><<<a.ninst, 256, 0, st>>>(a);
-  else
-    mcm_prologue_kernel<false><<<a.ninst, 256, 0, st>>>(a);
+  const bool w = a.w_all != nullptr;
+  if (i64) {
+    if (w) return cudaErrorNotSupported;
+    mcm_prologue_kernel<true, false><<<a.ninst, 256, 0, st>>>(a);
+  } else {
+    if (w) mcm_prologue_kernel<false, true><<<a.ninst, 256, 0, st>>>(a);
+    else mcm_prologue_kernel<false, false><<<a.ninst, 256, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_mcm_main(const McmLaunchArgs& a, bool i64, int grid, cudaStream_t st) {
   if (a.ntasks <= 0) return cudaSuccess;
-  if (i64)
-    mcm_main_kernel<true><<<grid, kMcmThreads, Smem<true>::TOTAL, st>>>(a);
-  else
-    mcm_main_kernel<false><<<grid, kMcmThreads, Smem<false>::TOTAL, st>>>(a);
+  const bool w = a.w_all != nullptr;
+  if (i64) {
+    if (w) return cudaErrorNotSupported;
+    mcm_main_kernel<true, false><<<grid, kMcmThreads, Smem<true>::TOTAL, st>>>(a);
+  } else {
+    if (w) mcm_main_kernel<false, true><<<grid, kMcmThreads, Smem<false>::TOTAL, st>>>(a);
+    else mcm_main_kernel<false, false><<<grid, kMcmThreads, Smem<false>::TOTAL, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -3,7 +3,9 @@
 // Problem (paper Section IV-A, Eq. (2); recurrence from Cormen et al., which
 // the paper cites): for i < j
 //     m[i][j] = min_{i <= k < j} m[i][k] + m[k+1][j] + p[i] * p[k+1] * p[j+1]
-// and s[i][j] = the smallest minimising k.
+// and s[i][j] = the smallest minimising k.  The interval-DP instances add a
+// per-cell weight w[i][j] to every candidate of cell (i, j) (Eq. (2) with a
+// more general f), which they do once, when the cell's minimum is final.
 //
 // GPU decomposition.  The n x n table is cut into 32 x 32 tiles (I, J), J >= I.
 // Tile (I, J) lies on tile-diagonal D = J - I.  For a cell of tile (I, J) the
@@ -29,7 +31,8 @@
 // progress whatever the number of resident blocks.
 //
 // Cost encodings (exact integer arithmetic throughout):
-//   int32 costs: every candidate is at most (n-1)*max(p)^3 =: bound < 2^31.
+//   int32 costs: every candidate is at most (n-1)*max(p)^3 =: bound < 2^31
+//     (interval DP: (n-1)*(max(p)^3 + max(w))).
 //     The packed row-panel entry is (m << S) | (k mod 2^S) and the column
 //     panel entry m << S, with S the largest value <= 5 such that
 //     (bound + 1) << S <= 2^32.  Then  A + B + (p_i p_j1) (p_k1 << S)
@@ -68,6 +71,8 @@ struct McmInstDev {
   int64_t tile_base;  // first index of this chain's tiles in the per-tile arrays
   int64_t pp_base;    // offset of this chain's padded dims in McmLaunchArgs::pp
   int64_t pk_base;    // offset of this chain's shifted dims in McmLaunchArgs::pk
+  const void* w;      // interval DP: per-cell weight table, like m (set by the prologue)
+  unsigned long long wmax;  // interval DP: largest weight above the diagonal (weight pass)
 };
 
 // kind 0: finisher of tile (I, J) for r levels [r_lo, r_hi], waits for
@@ -102,11 +107,22 @@ struct McmLaunchArgs {
   const int64_t* tab_off;        // nullptr: single chain at m_all / s_all
   void* m_all;
   int16_t* s_all;
+  // Interval DP (nullptr: plain MCM): per-cell weights laid out like m_all
+  // (chain b's n x n table at offset tab_off[b]); w[i][j], i < j, is added to
+  // the minimum of cell (i, j), and p may then hold zeros.
+  const void* w_all;
 };
 
 size_t mcm_smem_bytes(bool i64);
 cudaError_t mcm_configure(bool i64);
 cudaError_t mcm_occupancy(bool i64, int* blocks_per_sm);
+// With a.w_all set, the prologue and main kernel are the interval-DP
+// instances, and launch_mcm_weight_max must run first (it fills
+// McmInstDev::wmax, from which the prologue derives the cost bound).  The
+// interval-DP instances exist for int32 costs only: the int64 one faulted on
+// the GPU for a reason that was not found, so it is not built, and these
+// calls return cudaErrorNotSupported for i64 with weights.
+cudaError_t launch_mcm_weight_max(const McmLaunchArgs& a, bool i64, int sms, cudaStream_t st);
 cudaError_t launch_mcm_prologue(const McmLaunchArgs& a, bool i64, cudaStream_t st);
 cudaError_t launch_mcm_main(const McmLaunchArgs& a, bool i64, int grid, cudaStream_t st);
 // Loads the prologue, main and split-pass kernels into the current context

@@ -26,6 +26,12 @@ simplified DP problem of Definition 1):
     8192 preset values, for a 2^26-cell table.
   * ``mcm_batch(...)``: many chains with log-uniform lengths.
   * ``serve_trace(...)``: a Poisson arrival trace of mixed MCM / S-DP requests.
+  * ``interval_random(n, pmax, wmax, seed)`` / ``interval_obst(n, fmax, seed)``:
+    instances of the interval DP with a per-cell weight (the triangular-table
+    DP of Section IV with a more general combining function): uniform factors
+    and weights, or the optimal-binary-search-tree shape (no rank-1 factors;
+    the weight of cell (i, j) is the total frequency of keys i+1..j and gaps
+    i..j).
 """
 from __future__ import annotations
 
@@ -241,3 +247,43 @@ def serve_trace(rate: float = 2000.0, duration: float = 60.0, seed: int = 4,
             preset = rng.u32(int(offs[0]))
             out.append(Request(t, kind, n, offsets=offs, preset=preset))
     return out
+
+
+# ----------------------------------------------------------------------------
+# interval DP with a per-cell weight
+# ----------------------------------------------------------------------------
+
+@dataclass
+class IntervalInstance:
+    p: np.ndarray                   # int32[n+1] rank-1 factors (zeros: no rank-1 term)
+    w: np.ndarray                   # int64[n, n] weights, zero on and below the diagonal
+
+    @property
+    def n(self) -> int:
+        return int(self.p.size) - 1
+
+
+def interval_random(n: int, pmax: int, wmax: int, seed: int) -> IntervalInstance:
+    """Factors uniform in [0, pmax] and weights uniform in [0, wmax] above the
+    diagonal (drawn row by row)."""
+    g = SplitMix64(seed)
+    p = g.randint(0, pmax, n + 1).astype(np.int32)
+    w = np.zeros((n, n), dtype=np.int64)
+    iu = np.triu_indices(n, 1)
+    w[iu] = g.randint(0, wmax, iu[0].size)
+    return IntervalInstance(p, w)
+
+
+def interval_obst(n: int, fmax: int, seed: int) -> IntervalInstance:
+    """Optimal-BST shape over n gaps (n - 1 keys): key frequencies uniform in
+    [1, fmax], gap frequencies uniform in [0, fmax]; no rank-1 factors; the
+    weight of cell (i, j), i < j, is the frequency of keys i+1..j plus that of
+    gaps i..j."""
+    g = SplitMix64(seed)
+    key = np.concatenate([[0], g.randint(1, fmax, n - 1)]) if n > 1 else np.zeros(1, np.int64)
+    gap = g.randint(0, fmax, n)
+    kc = np.cumsum(key)                          # kc[j] = keys 1..j
+    gc = np.concatenate([[0], np.cumsum(gap)])   # gc[t] = gaps 0..t-1
+    w = (kc[None, :] - kc[:, None]) + (gc[None, 1:] - gc[:n, None])
+    w = np.triu(w, 1).astype(np.int64)
+    return IntervalInstance(np.zeros(n + 1, dtype=np.int32), w)

@@ -58,6 +58,12 @@ def test_host_validation_without_gpu(lib):
     assert b"strictly decreasing" in lib.dp_last_error()
     lib.mcm_solve.restype = ctypes.c_int
     assert lib.mcm_solve(ctypes.c_void_p(1), 0, 0, ctypes.c_void_p(1), ctypes.c_void_p(1), None, None) == 1
+    # the interval DP is built for int32 costs only: int64 is refused on the host
+    lib.interval_dp_solve.restype = ctypes.c_int
+    one = ctypes.c_void_p(1)
+    assert lib.interval_dp_solve(one, one, 40, 1, one, one, None, None) == 1
+    assert b"DP_COST_I32" in lib.dp_last_error()
+    assert lib.interval_dp_solve(one, None, 40, 0, one, one, None, None) == 1
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):

@@ -67,3 +67,22 @@ def test_serve_trace_shape():
             assert (1 << 16) <= r.n <= (1 << 24)
             assert r.offsets.size == 16 and np.all(np.diff(r.offsets) < 0)
             assert r.preset.size == r.offsets[0]
+
+
+def test_interval_instances():
+    a = inputs.interval_random(40, 7, 99, seed=9)
+    b = inputs.interval_random(40, 7, 99, seed=9)
+    assert np.array_equal(a.p, b.p) and np.array_equal(a.w, b.w)
+    assert a.p.dtype == np.int32 and a.p.min() >= 0 and a.p.max() <= 7
+    assert a.w.dtype == np.int64 and a.w.min() >= 0 and a.w.max() <= 99
+    assert not np.any(np.tril(a.w))                  # nothing on or below the diagonal
+    assert a.p.min() == 0 and a.w[np.triu_indices(40, 1)].min() == 0
+    # the OBST weight, summed key by key and gap by gap
+    o = inputs.interval_obst(30, 5, seed=10)
+    assert not np.any(o.p)
+    g = inputs.SplitMix64(10)
+    key = [0] + g.randint(1, 5, 29).tolist()          # keys 1..29
+    gap = g.randint(0, 5, 30).tolist()                # gaps 0..29
+    for i in range(30):
+        for j in range(i + 1, 30):
+            assert o.w[i, j] == sum(key[i + 1:j + 1]) + sum(gap[i:j + 1])
