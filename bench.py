@@ -339,6 +339,25 @@ def bench_sdp(dp, native, lib, dev, args):
                                      "achieved": cells * k / (kms / 1e3) / 1e9, "peak": smem_peak,
                                      "unit": "G words/s", "frac": cells * k / (kms / 1e3) / 1e9 / smem_peak,
                                      "per_unit": f"{k} window reads per cell"}}
+    # the paper's worst case for its pipeline (Section III-A): 32 consecutive
+    # offsets, here 1055 .. 1024 (same W = 1024 cells per step, same k)
+    cons = np.arange(1055, 1023, -1, dtype=np.int32)
+    st1 = np.zeros(big.n, dtype=np.uint32)
+    st1[:1055] = inputs.SplitMix64(6).u32(1055)
+    t1 = torch.from_numpy(st1.view(np.int32)).to(dev)
+    dp.sdp_solve(t1, cons, op="min")
+    dp.sync_status()
+    lib.dp_profile_begin()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        dp.sdp_solve(t1, cons, op="min")
+    torch.cuda.synchronize()
+    a, b, c, d = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+    native.check(lib.dp_profile_end(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    kms = c.value / max(d.value, 1)
+    res["consecutive_min"] = {"workload": "same n, k=32 consecutive offsets 1055..1024 (the paper's conflict worst "
+                                          "case), preset seed 6", "cells_per_s": (big.n - 1055) / (kms / 1e3),
+                              "kernel_ms": kms}
     return res
 
 
