@@ -204,17 +204,21 @@ __device__ __forceinline__ void seg_i32(const uint32_t* __restrict__ A, const ui
     uint32_t acc[4][2];
 #pragma unroll
     for (int r = 0; r < 4; ++r) acc[r][0] = acc[r][1] = 0xFFFFFFFFu;
+    // two splits per update: one three-way minimum for two candidates
 #pragma unroll
-    for (int kk = 0; kk < C; ++kk) {
-      const uint4 a = *reinterpret_cast<const uint4*>(A + (c0 + kk) * T + 4 * ty);
-      const uint2 b = *reinterpret_cast<const uint2*>(B + (c0 + kk) * T + 2 * tx);
-      const uint32_t pk = PK[c0 + kk];
-      const uint32_t av[4] = {a.x, a.y, a.z, a.w};
-      const uint32_t bv[2] = {b.x, b.y};
+    for (int kk = 0; kk < C; kk += 2) {
+      const uint4 a0 = *reinterpret_cast<const uint4*>(A + (c0 + kk) * T + 4 * ty);
+      const uint2 b0 = *reinterpret_cast<const uint2*>(B + (c0 + kk) * T + 2 * tx);
+      const uint4 a1 = *reinterpret_cast<const uint4*>(A + (c0 + kk + 1) * T + 4 * ty);
+      const uint2 b1 = *reinterpret_cast<const uint2*>(B + (c0 + kk + 1) * T + 2 * tx);
+      const uint32_t pk0 = PK[c0 + kk], pk1 = PK[c0 + kk + 1];
+      const uint32_t av0[4] = {a0.x, a0.y, a0.z, a0.w}, av1[4] = {a1.x, a1.y, a1.z, a1.w};
+      const uint32_t bv0[2] = {b0.x, b0.y}, bv1[2] = {b1.x, b1.y};
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) acc[r][c] = umin(acc[r][c], P[r][c] * pk + av[r] + bv[c]);
+        for (int c = 0; c < 2; ++c)
+          acc[r][c] = __vimin3_u32(acc[r][c], P[r][c] * pk0 + av0[r] + bv0[c], P[r][c] * pk1 + av1[r] + bv1[c]);
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -579,7 +583,10 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
                       const int q = (1 + s4 + r) & 3;
                       const E cc = u4.v[r] + xc + wv[r] * pkc;
                       const E cr = x4.v[r] + R[q] + wv[r] * (E)P[q];
-                      m[r] = umin(m[r], umin(cc, cr));
+                      if constexpr (I64)
+                        m[r] = umin(m[r], umin(cc, cr));
+                      else
+                        m[r] = __vimin3_u32(m[r], cc, cr);
                     }
                     // the lane's cell on diagonal e + 1 is final now
                     const int rr = c0 - e;
