@@ -69,6 +69,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   return true;
 }
 
+// mbar_wait with the sleep between polls capped at cap_ns, for waits on the
+// critical path (a long sleep delays the wake-up after the data lands).
+__device__ __forceinline__ bool mbar_wait_cap(uint64_t* bar, uint32_t parity, long long limit, uint32_t cap_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  uint32_t polls = 0, backoff = 16;
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > limit) return false;
+    if (++polls > 4) {
+      __nanosleep(backoff);
+      backoff = backoff < cap_ns ? backoff * 2 : cap_ns;
+    }
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // 1-D bulk copy global -> shared (TMA), completion counted on an mbarrier.
 // dst, src 16-byte aligned; bytes a multiple of 16.

@@ -12,6 +12,7 @@ namespace dpk {
 namespace {
 
 constexpr int T = kTile;
+constexpr uint32_t kFinPollNs = 64;  // finisher waits (int32): longest sleep between polls
 constexpr int kDiagRows = 2 * T;  // cell diagonals e = lj - li in [-31, 31] (dI = e + 31), one spare row
 
 template <bool I64>
@@ -431,7 +432,14 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
         const int st = u % kStages;
         const uint32_t round = u / kStages;
         if (!ok) return;
-        if (!mbar_wait(&bar_full[g * kStages + st], round & 1u, limit)) {
+        bool got;
+        if constexpr (I64) {
+          got = mbar_wait(&bar_full[g * kStages + st], round & 1u, limit);
+        } else {  // a finisher's segments are on the critical path: poll more often
+          got = finisher ? mbar_wait_cap(&bar_full[g * kStages + st], round & 1u, limit, kFinPollNs)
+                         : mbar_wait(&bar_full[g * kStages + st], round & 1u, limit);
+        }
+        if (!got) {
           set_status(status, DP_ETIMEOUT);
           ok = false;
           return;
@@ -491,7 +499,11 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
           }
         }
         const uint32_t fpar = fin_cnt & 1u;
-        const bool fin_ok = mbar_wait(bar_fin, fpar, limit);
+        bool fin_ok;
+        if constexpr (I64)
+          fin_ok = mbar_wait(bar_fin, fpar, limit);
+        else
+          fin_ok = mbar_wait_cap(bar_fin, fpar, limit, kFinPollNs);
         if (!fin_ok) set_status(status, DP_ETIMEOUT);
         const bool go = bar_compute_and(fin_ok && *reinterpret_cast<volatile int32_t*>(status) == 0);
         const int shiftv = I64 ? 16 : S;
