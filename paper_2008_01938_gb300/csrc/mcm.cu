@@ -539,11 +539,27 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
               const E bnd = (finU[(T - 1) * T + li] >> shiftv) + brow + wv[r] * pI32;
               m[r] = umin((E)(cb[r] >> KB), bnd);
             }
-            for (int idx = tid; idx < SM::kRows * T; idx += kComputeThreads) {
-              const int q = idx >> 5, x = idx & 31, t = q - SM::kRowOff;
-              const bool in = t >= 0 && t <= T - 2;
-              Up[q * SM::UPW + x] = in ? (finU[t * T + x] >> shiftv) : (E)0;
-              Lp[idx] = in ? (finL[t * T + x] >> shiftv) : (E)0;
+            if constexpr (!I64) {
+              // 16-byte vectors: 8 per row, 3 per thread (all row pitches are 16-byte multiples)
+              for (int v = tid; v < SM::kRows * T / 4; v += kComputeThreads) {
+                const int q = v >> 3, x = (v & 7) * 4, t = q - SM::kRowOff;
+                uint4 uu = make_uint4(0u, 0u, 0u, 0u), ll = make_uint4(0u, 0u, 0u, 0u);
+                if (t >= 0 && t <= T - 2) {
+                  const uint4 fu = *reinterpret_cast<const uint4*>(finU + t * T + x);
+                  const uint4 fl = *reinterpret_cast<const uint4*>(finL + t * T + x);
+                  uu = make_uint4(fu.x >> S, fu.y >> S, fu.z >> S, fu.w >> S);
+                  ll = make_uint4(fl.x >> S, fl.y >> S, fl.z >> S, fl.w >> S);
+                }
+                *reinterpret_cast<uint4*>(Up + q * SM::UPW + x) = uu;
+                *reinterpret_cast<uint4*>(Lp + q * T + x) = ll;
+              }
+            } else {
+              for (int idx = tid; idx < SM::kRows * T; idx += kComputeThreads) {
+                const int q = idx >> 5, x = idx & 31, t = q - SM::kRowOff;
+                const bool in = t >= 0 && t <= T - 2;
+                Up[q * SM::UPW + x] = in ? (finU[t * T + x] >> shiftv) : (E)0;
+                Lp[idx] = in ? (finL[t * T + x] >> shiftv) : (E)0;
+              }
             }
             if constexpr (!SM::kXOut) {
               for (int idx = tid; idx < kDiagRows * T; idx += kComputeThreads) {
