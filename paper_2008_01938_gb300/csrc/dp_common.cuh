@@ -159,4 +159,28 @@ __device__ __forceinline__ bool wait_flag_geq(const int32_t* flag, int32_t targe
   }
 }
 
+// wait_flag_geq with the sleep between polls capped at CAP ns (int32 MCM
+// instances: every flag wait there is, directly or through the tasks that
+// follow, on the chain of tile-diagonals).
+template <uint32_t CAP>
+__device__ __forceinline__ bool wait_flag_geq_cap(const int32_t* flag, int32_t target, long long limit,
+                                                  int32_t* status) {
+  if (ld_acquire(flag) >= target) return true;
+  const long long t0 = clock64();
+  uint32_t backoff = CAP < 32 ? CAP : 32;
+  while (true) {
+    if (ld_relaxed(flag) >= target) {
+      fence_acquire_gpu();
+      return true;
+    }
+    if (clock64() - t0 > limit) {
+      set_status(status, DP_ETIMEOUT);
+      return false;
+    }
+    if (*reinterpret_cast<volatile const int32_t*>(status) != 0) return false;
+    __nanosleep(backoff);
+    backoff = backoff < CAP ? backoff * 2 : CAP;
+  }
+}
+
 }  // namespace dpk

@@ -12,7 +12,17 @@ namespace dpk {
 namespace {
 
 constexpr int T = kTile;
-constexpr uint32_t kFinPollNs = 64;  // finisher waits (int32): longest sleep between polls
+constexpr uint32_t kFinPollNs = 64;   // finisher mbarrier waits (int32): longest sleep between polls
+constexpr uint32_t kFlagPollNs = 32;  // flag and counter waits (int32): longest sleep between polls
+
+// Flag wait of the int32 instances (shorter polling), or the common one.
+template <bool I64>
+__device__ __forceinline__ bool wait_flag(const int32_t* flag, int32_t target, long long limit, int32_t* status) {
+  if constexpr (I64)
+    return wait_flag_geq(flag, target, limit, status);
+  else
+    return wait_flag_geq_cap<kFlagPollNs>(flag, target, limit, status);
+}
 constexpr int kDiagRows = 2 * T;  // cell diagonals e = lj - li in [-31, 31] (dI = e + 31), one spare row
 
 template <bool I64>
@@ -354,9 +364,9 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
           const int st = u % kStages;
           const uint32_t round = u / kStages;
           if (!ok) return;
-          ok = wait_flag_geq(a.flags + tile_index(inst, I, K), 1, limit, status) &&
-               wait_flag_geq(a.flags + tile_index(inst, K, J), 1, limit, status) &&
-               wait_flag_geq(a.flags + tile_index(inst, K + 1, J), 1, limit, status);
+          ok = wait_flag<I64>(a.flags + tile_index(inst, I, K), 1, limit, status) &&
+               wait_flag<I64>(a.flags + tile_index(inst, K, J), 1, limit, status) &&
+               wait_flag<I64>(a.flags + tile_index(inst, K + 1, J), 1, limit, status);
           if (!ok) return;
           fence_proxy_async_global();
           if (!mbar_wait(&bar_empty[g * kStages + st], (round & 1u) ^ 1u, limit)) {
@@ -376,10 +386,10 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
         });
         if (finisher && ok) {
           if (D >= 1)
-            ok = wait_flag_geq(a.flags + tile_index(inst, I, I), 1, limit, status) &&
-                 wait_flag_geq(a.flags + tile_index(inst, J, J), 1, limit, status) &&
-                 wait_flag_geq(a.flags + tile_index(inst, I + 1, J), 1, limit, status);
-          if (ok && task.nparts > 0) ok = wait_flag_geq(a.counters + tidx, task.nparts, limit, status);
+            ok = wait_flag<I64>(a.flags + tile_index(inst, I, I), 1, limit, status) &&
+                 wait_flag<I64>(a.flags + tile_index(inst, J, J), 1, limit, status) &&
+                 wait_flag<I64>(a.flags + tile_index(inst, I + 1, J), 1, limit, status);
+          if (ok && task.nparts > 0) ok = wait_flag<I64>(a.counters + tidx, task.nparts, limit, status);
           if (ok) {
             fence_proxy_async_global();
             uint32_t bytes = 3 * 128;
