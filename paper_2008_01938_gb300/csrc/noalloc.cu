@@ -62,8 +62,8 @@ static_assert(kMaxNt == 32, "the queue builder maps one warp lane to each tile r
 __device__ __align__(256) uint8_t g_mcm_scratch[kScratchBytes];
 
 // The work split of a tile on tile-diagonal D (see kLevelsPerPart): bulk
-// part q covers levels [rmin + q*kLevelsPerPart, r1(q)], r1(q) = min(that + 3,
-// fin_lo - 1); the finisher keeps [fin_lo, D - 1].
+// part q covers levels [rmin + q*kLevelsPerPart, r1(q)], r1(q) = min(that +
+// kLevelsPerPart - 1, fin_lo - 1); the finisher keeps [fin_lo, D - 1].
 struct TileSplit {
   int rmin, fin_lo, nparts;
 };
