@@ -288,6 +288,8 @@ def run_gb300(args):
         extras = set(args.extras.split(","))
         if "sdp" in extras:
             out["sdp"] = bench_sdp(dp, native, lib, dev, args)
+        if "small" in extras:
+            out["small"] = bench_small(dp, native, lib, dev, args)
         if "interval" in extras:
             out["interval"] = bench_interval(dp, native, lib, dev, args)
         if "batched" in extras:
@@ -411,6 +413,33 @@ def bench_interval(dp, native, lib, dev, args):
             "parity_sha256_ok": parity, "l2": "flushed between solves (outside the timed events)"}
 
 
+def bench_small(dp, native, lib, dev, args):
+    """Latency of the 128-matrix chain (dims U[1,32], seed 0): 127
+    tile-diagonal cells in 4 tile-diagonals, far from any throughput bound."""
+    import torch
+    from paper_2008_01938_gb300 import inputs
+    p = torch.from_numpy(inputs.mcm_small()).to(dev)
+    m = torch.empty((128, 128), dtype=torch.int32, device=dev)
+    s = torch.empty((128, 128), dtype=torch.int16, device=dev)
+    for _ in range(10):
+        dp.mcm_solve(p, "i32", m, s)
+    dp.sync_status()
+    reps = 200
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a_, b_ in ev:
+        a_.record(stream)
+        dp.mcm_solve(p, "i32", m, s)
+        b_.record(stream)
+    torch.cuda.synchronize()
+    dp.sync_status()
+    t = sorted(a_.elapsed_time(b_) for a_, b_ in ev)
+    evals = (128 ** 3 - 128) // 6
+    return {"workload": "MCM n=128 chain, dims U[1,32] seed 0, int32, one mcm_solve (prologue + main kernel)",
+            "median_us": t[reps // 2] * 1e3, "p90_us": t[(9 * reps) // 10] * 1e3,
+            "split_evals_per_s": evals / (t[reps // 2] / 1e3)}
+
+
 def bench_batched(dp, native, lib, dev, args):
     import numpy as np
     import torch
@@ -441,6 +470,16 @@ def bench_batched(dp, native, lib, dev, args):
     torch.cuda.synchronize()
     dp.sync_status()
     t_graph = e0.elapsed_time(e1) / reps / 1e3
+    # the same plan launched directly on the stream (no graph)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        e0.record(st)
+        for _ in range(reps):
+            plan.solve(p_all, p_off, tab_off, m_all, s_all, stream=st)
+        e1.record(st)
+    torch.cuda.synchronize()
+    dp.sync_status()
+    t_nograph = e0.elapsed_time(e1) / reps / 1e3
     gold = os.path.join(ROOT, "tests", "golden", "fullsize.json")
     parity = None
     if os.path.exists(gold):
@@ -465,6 +504,7 @@ def bench_batched(dp, native, lib, dev, args):
     plan.destroy()
     return {"workload": "10,000 chains, n log-uniform [8,512], dims U[1,1000] seed 3, int64 costs",
             "split_evals": total, "graph_evals_per_s": total / t_graph, "graph_ms": t_graph * 1e3,
+            "no_graph_ms": t_nograph * 1e3,
             "plain_loop_evals_per_s": total / t_plain, "plain_loop_ms": t_plain * 1e3,
             "speedup_vs_plain": t_plain / t_graph, "parity_sha256_ok": parity,
             "autotuned": {"levels_per_bulk_task": tuned[0], "blocks_per_sm": tuned[1]}}
@@ -581,8 +621,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--extras", default="sdp,interval,batched,serve",
-                    help="comma-separated sections after the headline: sdp, interval, batched, serve")
+    ap.add_argument("--extras", default="small,sdp,interval,batched,serve",
+                    help="comma-separated sections after the headline: small, sdp, interval, batched, serve")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     args = ap.parse_args()
