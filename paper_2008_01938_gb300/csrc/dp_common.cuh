@@ -159,9 +159,10 @@ __device__ __forceinline__ bool wait_flag_geq(const int32_t* flag, int32_t targe
   }
 }
 
-// wait_flag_geq with the sleep between polls capped at CAP ns (int32 MCM
-// instances: every flag wait there is, directly or through the tasks that
-// follow, on the chain of tile-diagonals).
+// wait_flag_geq with the sleep between polls capped at CAP ns and acquire
+// loads for the polls (int32 MCM instances: every flag wait there is,
+// directly or through the tasks that follow, on the chain of
+// tile-diagonals).
 template <uint32_t CAP>
 __device__ __forceinline__ bool wait_flag_geq_cap(const int32_t* flag, int32_t target, long long limit,
                                                   int32_t* status) {
@@ -169,10 +170,7 @@ __device__ __forceinline__ bool wait_flag_geq_cap(const int32_t* flag, int32_t t
   const long long t0 = clock64();
   uint32_t backoff = CAP < 32 ? CAP : 32;
   while (true) {
-    if (ld_relaxed(flag) >= target) {
-      fence_acquire_gpu();
-      return true;
-    }
+    if (ld_acquire(flag) >= target) return true;  // acquire polls: no fence after the flip
     if (clock64() - t0 > limit) {
       set_status(status, DP_ETIMEOUT);
       return false;
