@@ -258,9 +258,16 @@ def run_gb300(args):
                                             ctypes.c_void_p(mh_t.data_ptr()), ctypes.c_void_p(sh_t.data_ptr()), sp))
         barrier()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
+        direct = bool(lib.dp_test_host_range_device_address(ctypes.c_void_p(mh_t.data_ptr()),
+                                                           mh_t.numel() * 4, 1))
+        e2e_parity = (None if parity is None else
+                      hashlib.sha256(mh_t.numpy().astype("<i4").tobytes()).hexdigest() == g["m_sha256"])
         e2e = {"value": world * EVALS_4096 / e2e_s, "unit": "split-evals/s",
                "h2d_bytes_per_step": (N_MCM + 1) * 4, "d2h_bytes_per_step": N_MCM * N_MCM * (4 + 2),
-               "ms_per_step": e2e_s * 1e3, "note": "includes the 256 MiB L2 flush write per step"}
+               "ms_per_step": e2e_s * 1e3, "parity_sha256_ok": e2e_parity,
+               "d2h": ("kernel stores into the pinned host tables" if direct
+                       else "copy after the solve"),
+               "note": "includes the 256 MiB L2 flush write per step"}
 
     peak = SM_COUNT * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     achieved = INT_OPS_PER_EVAL * EVALS_4096 / (kernel_ms / 1e3) / 1e12

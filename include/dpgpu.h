@@ -164,9 +164,15 @@ dp_status mcm_solve_noalloc(const int32_t *p, int32_t n, int32_t *m, int16_t *s,
  * levels; NULL s or steps (n > 1) or n outside [1, 32767] return DP_EINVAL. */
 dp_status mcm_traceback(const int16_t *s, int32_t n, int32_t *steps, int32_t *status_dev, void *stream);
 
-/* Same computation with HOST buffers: copies p (n+1 int32) to the device,
- * solves, copies m and s back, and waits for completion.  Host buffers may be
- * pageable or pinned (pinned is faster). */
+/* Same computation with HOST buffers (p: n+1 int32, m: n*n cost elements,
+ * s: n*n int16, row-major), waiting for completion before it returns.
+ * Page-locked m and s (cudaHostAlloc, cudaHostRegister without the read-only
+ * flag) that the current device can address, each inside one allocation, are
+ * written by the kernel in place: the tables reach host memory while the
+ * solve runs and no copy follows it.  A page-locked p is read in place.  Any
+ * other buffer is staged through device memory with a copy before (p) or
+ * after (m, s) the solve.  The caller owns all three buffers; their sizes are
+ * not checked beyond the allocation test above. */
 dp_status mcm_solve_host(const int32_t *p_host, int32_t n, dp_cost ct, void *m_host,
                          int16_t *s_host, void *stream);
 

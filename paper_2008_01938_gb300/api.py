@@ -148,7 +148,11 @@ def mcm_traceback(s, steps=None, status=None, stream=None):
 
 
 def mcm_solve_host(p, cost="i32", m=None, s=None, stream=None):
-    """Host-buffer form: numpy (or pinned torch CPU) dims in, tables out."""
+    """Host-buffer form: numpy arrays or torch CPU tensors in and out.
+
+    When m and s are page-locked (torch ``pin_memory()``, cudaHostAlloc) the
+    kernel writes the tables straight into them; other buffers are filled by
+    a copy after the solve."""
     lib = native.load()
     ct = _cost(cost)
     p = np.ascontiguousarray(np.asarray(p, dtype=np.int32)) if not hasattr(p, "data_ptr") else p
@@ -158,6 +162,20 @@ def mcm_solve_host(p, cost="i32", m=None, s=None, stream=None):
         m = np.empty((n, n), dtype=mdt)
     if s is None:
         s = np.empty((n, n), dtype=np.int16)
+
+    def host_buf(x, dt, name, count):
+        if isinstance(x, np.ndarray):
+            ok = x.dtype == dt and x.flags.c_contiguous and x.size == count
+        else:
+            tdt = {np.int16: "int16", np.int32: "int32", np.int64: "int64"}[dt]
+            ok = (x.device.type == "cpu" and x.is_contiguous() and x.numel() == count
+                  and x.dtype == getattr(_torch(), tdt))
+        if not ok:
+            raise ValueError(f"{name} must be a contiguous host {np.dtype(dt).name} buffer of {count} entries")
+
+    host_buf(p, np.int32, "p", n + 1)
+    host_buf(m, mdt, "m", n * n)
+    host_buf(s, np.int16, "s", n * n)
 
     def hp(x):
         return ctypes.c_void_p(x.ctypes.data) if isinstance(x, np.ndarray) else ctypes.c_void_p(x.data_ptr())

@@ -1,5 +1,6 @@
 // api.cu -- host side of the C ABI declared in include/dpgpu.h: argument
 // validation, the diagonal-ordered MCM work queue, workspaces and launches.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -396,6 +397,51 @@ struct SdpPlan {
   int32_t* d_offs = nullptr;
 };
 
+// Device address of the host range [ptr, ptr + bytes) if the current device
+// can access it in place: page-locked memory (cudaHostAlloc, cudaHostRegister)
+// mapped for this device, the whole range inside one allocation, and
+// writable by the device when `writable`.  nullptr otherwise (pageable
+// memory, a range that leaves its allocation, or a query the driver does not
+// answer), in which case the caller stages the data through device memory.
+using PointerAttributeFn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+PointerAttributeFn pointer_attribute_fn() {
+  static const PointerAttributeFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<PointerAttributeFn>(f);
+  }();
+  return fn;
+}
+
+void* host_range_device_address(const void* ptr, size_t bytes, bool writable) {
+  if (!ptr || bytes == 0) return nullptr;
+  const PointerAttributeFn attr = pointer_attribute_fn();
+  if (!attr) return nullptr;
+  const uint8_t* first = static_cast<const uint8_t*>(ptr);
+  const uint8_t* last = first + (bytes - 1);
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, first) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (pa.type != cudaMemoryTypeHost || !pa.devicePointer) return nullptr;
+  unsigned long long id0 = 0, id1 = 0;
+  unsigned int access = 0;
+  if (attr(&id0, CU_POINTER_ATTRIBUTE_BUFFER_ID, reinterpret_cast<CUdeviceptr>(first)) != CUDA_SUCCESS ||
+      attr(&id1, CU_POINTER_ATTRIBUTE_BUFFER_ID, reinterpret_cast<CUdeviceptr>(last)) != CUDA_SUCCESS ||
+      attr(&access, CU_POINTER_ATTRIBUTE_ACCESS_FLAGS, reinterpret_cast<CUdeviceptr>(first)) != CUDA_SUCCESS)
+    return nullptr;
+  if (id0 == 0 || id0 != id1) return nullptr;
+  const unsigned int need = writable ? CU_POINTER_ATTRIBUTE_ACCESS_FLAG_READWRITE : CU_POINTER_ATTRIBUTE_ACCESS_FLAG_READ;
+  if ((access & need) != need) return nullptr;
+  return pa.devicePointer;
+}
+
 dp_status mcm_solve_impl(const int32_t* p, int32_t n, dp_cost ct, void* m, int16_t* s, int32_t* status_dev,
                          cudaStream_t st, long long limit_override, int32_t drop_task, const void* w = nullptr) {
   const char* who = w ? "interval_dp_solve" : "mcm_solve";
@@ -510,20 +556,29 @@ dp_status mcm_solve_host(const int32_t* p_host, int32_t n, dp_cost ct, void* m_h
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t es = ct == DP_COST_I64 ? 8 : 4;
   const size_t nn = (size_t)n * n;
+  // Page-locked tables the device may write are the kernel's outputs
+  // themselves: the results reach host memory while the solve runs, and no
+  // copy follows it.  Page-locked dims are read in place.
+  void* m_dev = host_range_device_address(m_host, nn * es, true);
+  void* s_dev = m_dev ? host_range_device_address(s_host, nn * 2, true) : nullptr;
+  const bool direct = m_dev && s_dev;
+  const int32_t* p_dev = static_cast<const int32_t*>(host_range_device_address(p_host, (size_t)(n + 1) * 4, false));
   uint8_t* buf = nullptr;
-  const size_t pb = align_up((size_t)(n + 1) * 4, 256), mb = align_up(nn * es, 256), sb = align_up(nn * 2, 256);
+  const size_t pb = p_dev ? 0 : align_up((size_t)(n + 1) * 4, 256);
+  const size_t mb = direct ? 0 : align_up(nn * es, 256), sb = direct ? 0 : align_up(nn * 2, 256);
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), pb + mb + sb + 256, st);
   if (e != cudaSuccess) return fail_cuda(e, "mcm_solve_host: allocation");
   int32_t* d_status = reinterpret_cast<int32_t*>(buf + pb + mb + sb);
   dp_status rc = DP_OK;
   if ((e = cudaMemsetAsync(d_status, 0, 4, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(buf, p_host, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+      (!p_dev && (e = cudaMemcpyAsync(buf, p_host, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)) {
     rc = fail_cuda(e, "mcm_solve_host: upload");
   }
   if (rc == DP_OK)
-    rc = mcm_solve_impl(reinterpret_cast<int32_t*>(buf), n, ct, buf + pb, reinterpret_cast<int16_t*>(buf + pb + mb),
-                        d_status, st, 0, -1);
-  if (rc == DP_OK) {
+    rc = mcm_solve_impl(p_dev ? p_dev : reinterpret_cast<int32_t*>(buf), n, ct, direct ? m_dev : buf + pb,
+                        direct ? static_cast<int16_t*>(s_dev) : reinterpret_cast<int16_t*>(buf + pb + mb), d_status,
+                        st, 0, -1);
+  if (rc == DP_OK && !direct) {
     if ((e = cudaMemcpyAsync(m_host, buf + pb, nn * es, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(s_host, buf + pb + mb, nn * 2, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       rc = fail_cuda(e, "mcm_solve_host: download");
@@ -532,6 +587,12 @@ dp_status mcm_solve_host(const int32_t* p_host, int32_t n, dp_cost ct, void* m_h
   cudaFreeAsync(buf, st);
   if (rc == DP_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = fail_cuda(e, "mcm_solve_host: sync");
   return rc;
+}
+
+// Test hook: the device address mcm_solve_host would use for a host range
+// (nullptr: the range goes through a device copy).
+void* dp_test_host_range_device_address(const void* ptr, size_t bytes, int writable) {
+  return host_range_device_address(ptr, bytes, writable != 0);
 }
 
 dp_status mcm_plan_create(int32_t batch, const int32_t* n_host, dp_cost ct, void** plan) {

@@ -94,6 +94,55 @@ def test_host_buffer_entry_point(dp):
     assert np.array_equal(m, om.astype(np.int32)) and np.array_equal(s, os_)
 
 
+def _host_address(dp, x, writable):
+    import ctypes
+    from paper_2008_01938_gb300 import native
+    lib = native.load()
+    nbytes = x.numel() * x.element_size() if hasattr(x, "numel") else x.nbytes
+    ptr = x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+    return lib.dp_test_host_range_device_address(ctypes.c_void_p(ptr), nbytes, int(writable))
+
+
+@pytest.mark.parametrize("cost,n", [("i32", 1), ("i32", 33), ("i32", 97), ("i32", 150), ("i64", 70), ("i64", 129)])
+def test_host_entry_point_pinned_tables(dp, cost, n):
+    """Page-locked m and s: the kernel writes them in place (no copy after the
+    solve); the tables match the oracle exactly."""
+    import torch
+    hi = 32 if cost == "i32" else 1000
+    p_np = inputs.mcm_dims(n, 1, hi, seed=40 + n)
+    p = torch.from_numpy(p_np).pin_memory()
+    tdt = torch.int32 if cost == "i32" else torch.int64
+    m = torch.full((n, n), 7, dtype=tdt).pin_memory()
+    s = torch.full((n, n), 7, dtype=torch.int16).pin_memory()
+    assert _host_address(dp, m, True) and _host_address(dp, s, True) and _host_address(dp, p, False)
+    dp.mcm_solve_host(p, cost=cost, m=m, s=s)
+    om, os_ = oracle.mcm(p_np)
+    assert np.array_equal(m.numpy(), om.astype(m.numpy().dtype)) and np.array_equal(s.numpy(), os_)
+
+
+def test_host_entry_point_mixed_buffers(dp):
+    """Pinned m with pageable s (and pageable dims) goes through the copy path."""
+    import torch
+    p_np = inputs.mcm_dims(120, 1, 32, seed=12)
+    m = torch.zeros((120, 120), dtype=torch.int32).pin_memory()
+    s = np.zeros((120, 120), np.int16)
+    assert not _host_address(dp, s, True) and not _host_address(dp, p_np, False)
+    dp.mcm_solve_host(p_np, cost="i32", m=m, s=s)
+    om, os_ = oracle.mcm(p_np)
+    assert np.array_equal(m.numpy(), om.astype(np.int32)) and np.array_equal(s, os_)
+
+
+def test_host_range_outside_allocation(dp):
+    """A range that runs past its page-locked allocation is not used in place."""
+    import torch
+    from paper_2008_01938_gb300 import native
+    import ctypes
+    x = torch.zeros(1 << 20, dtype=torch.uint8).pin_memory()
+    lib = native.load()
+    assert lib.dp_test_host_range_device_address(ctypes.c_void_p(x.data_ptr()), 1 << 20, 1)
+    assert not lib.dp_test_host_range_device_address(ctypes.c_void_p(x.data_ptr()), 1 << 40, 1)
+
+
 def test_status_word_argument(dp):
     import torch
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
