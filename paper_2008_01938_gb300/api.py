@@ -255,13 +255,23 @@ def sdp_solve(st, offsets, op="min", n=None, status=None, stream=None):
 
 
 def sdp_solve_host(st, offsets, op="min", stream=None):
-    """Host form: ``st`` is a numpy uint32 array of length n with the preset
-    in front; it is filled in place."""
+    """Host form: ``st`` holds the n table words (preset in front) and is
+    filled in place.  It is a contiguous numpy uint32 array or a contiguous
+    torch CPU tensor of 32-bit integers; a page-locked one (``pin_memory()``)
+    is written by the kernel directly when the window fits on chip."""
     lib = native.load()
-    if st.dtype != np.uint32 or not st.flags.c_contiguous:
-        raise TypeError("st must be a contiguous numpy uint32 array")
+    if isinstance(st, np.ndarray):
+        if st.dtype != np.uint32 or not st.flags.c_contiguous:
+            raise TypeError("st must be a contiguous numpy uint32 array")
+        ptr, n = st.ctypes.data, int(st.size)
+    else:
+        torch = _torch()
+        dts = [torch.int32] + ([torch.uint32] if hasattr(torch, "uint32") else [])
+        if st.device.type != "cpu" or not st.is_contiguous() or st.dtype not in dts:
+            raise TypeError("st must be a contiguous CPU tensor of 32-bit integers")
+        ptr, n = st.data_ptr(), int(st.numel())
     a = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
-    check(lib.sdp_solve_host(ctypes.c_void_p(st.ctypes.data), int(st.size), ctypes.c_void_p(a.ctypes.data),
+    check(lib.sdp_solve_host(ctypes.c_void_p(ptr), n, ctypes.c_void_p(a.ctypes.data),
                              int(a.size), _op(op), _stream_ptr(stream)))
     return st
 

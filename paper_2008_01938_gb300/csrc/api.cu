@@ -759,8 +759,22 @@ dp_status sdp_solve_host(uint32_t* ST_host, int64_t n, const int32_t* a, int32_t
   if (rc != DP_OK) return rc;
   if (n <= a[0]) return DP_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  // A page-locked table the device may write is solved in place when the
+  // window fits the shared-memory ring: the kernel then reads the table only
+  // for the preset and writes every other cell once, so nothing is copied.
+  // (A wider window is read from the table at every step and is staged in
+  // device memory instead.)
+  int threads = 0, ring_log2 = 0;
+  sdp_shape(a[0], a[k - 1], &threads, &ring_log2);
+  if (void* in_place = ring_log2 > 0 ? host_range_device_address(ST_host, (size_t)n * 4, true) : nullptr) {
+    rc = sdp_solve(static_cast<uint32_t*>(in_place), n, a, k, op, nullptr, stream);
+    if (rc == DP_OK) rc = dp_sync_status(stream, nullptr);
+    if (rc == DP_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = fail_cuda(e, "sdp_solve_host: sync");
+    return rc;
+  }
   uint32_t* d = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), (size_t)n * 4, st);
+  e = cudaMallocAsync(reinterpret_cast<void**>(&d), (size_t)n * 4, st);
   if (e != cudaSuccess) return fail_cuda(e, "sdp_solve_host: allocation");
   if ((e = cudaMemcpyAsync(d, ST_host, (size_t)a[0] * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     rc = fail_cuda(e, "sdp_solve_host: upload");

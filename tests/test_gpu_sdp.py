@@ -135,6 +135,23 @@ def test_host_entry_point(dp):
     assert np.array_equal(st, oracle.sdp(inst.preset, inst.n, inst.offsets, "min"))
 
 
+@pytest.mark.parametrize("op,amax", [("min", 2000), ("add", 2000), ("min", 40000)])
+def test_host_entry_point_pinned(dp, op, amax):
+    """Page-locked table: solved in place when the window fits the on-chip
+    ring (a_1 <= 2000 here), staged through device memory when it does not
+    (a_1 near 40000); either way identical to the oracle."""
+    import ctypes
+    import torch
+    from paper_2008_01938_gb300 import native
+    inst = inputs.sdp_random(n=90001, k=12, amin=300, amax=amax, seed=13 + amax)
+    st = torch.zeros(inst.n, dtype=torch.int32).pin_memory()
+    st.numpy().view(np.uint32)[:inst.offsets[0]] = inst.preset
+    lib = native.load()
+    assert lib.dp_test_host_range_device_address(ctypes.c_void_p(st.data_ptr()), inst.n * 4, 1)
+    dp.sdp_solve_host(st, inst.offsets, op=op)
+    assert np.array_equal(st.numpy().view(np.uint32), oracle.sdp(inst.preset, inst.n, inst.offsets, op))
+
+
 @pytest.mark.parametrize("op", ["min", "add"])
 def test_batched_parity(dp, op):
     import torch
