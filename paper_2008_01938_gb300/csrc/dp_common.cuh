@@ -181,4 +181,26 @@ __device__ __forceinline__ bool wait_flag_geq_cap(const int32_t* flag, int32_t t
   }
 }
 
+// Waits until f[x] >= target[x] for every x < N (int32 MCM instances).  The
+// first test issues all N acquire loads at once, so the words already set
+// cost one round trip together rather than one each; any still short are
+// then polled one at a time with wait_flag_geq_cap.  A target of 0 is met at
+// once.  Every word is read by an acquire load, so no fence follows.
+template <uint32_t CAP, int N>
+__device__ __forceinline__ bool wait_flags_geq_cap(const int32_t* const (&f)[N], const int32_t (&target)[N],
+                                                   long long limit, int32_t* status) {
+  int32_t v[N];
+#pragma unroll
+  for (int x = 0; x < N; ++x) v[x] = ld_acquire(f[x]);
+  bool all = true;
+#pragma unroll
+  for (int x = 0; x < N; ++x) all = all && v[x] >= target[x];
+  if (!all) {
+#pragma unroll
+    for (int x = 0; x < N; ++x)
+      if (v[x] < target[x] && !wait_flag_geq_cap<CAP>(f[x], target[x], limit, status)) return false;
+  }
+  return true;
+}
+
 }  // namespace dpk

@@ -364,9 +364,16 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
           const int st = u % kStages;
           const uint32_t round = u / kStages;
           if (!ok) return;
-          ok = wait_flag<I64>(a.flags + tile_index(inst, I, K), 1, limit, status) &&
-               wait_flag<I64>(a.flags + tile_index(inst, K, J), 1, limit, status) &&
-               wait_flag<I64>(a.flags + tile_index(inst, K + 1, J), 1, limit, status);
+          if constexpr (I64) {
+            ok = wait_flag<I64>(a.flags + tile_index(inst, I, K), 1, limit, status) &&
+                 wait_flag<I64>(a.flags + tile_index(inst, K, J), 1, limit, status) &&
+                 wait_flag<I64>(a.flags + tile_index(inst, K + 1, J), 1, limit, status);
+          } else {  // the three tiles' flags in one round trip when they are set
+            const int32_t* const fl[3] = {a.flags + tile_index(inst, I, K), a.flags + tile_index(inst, K, J),
+                                          a.flags + tile_index(inst, K + 1, J)};
+            const int32_t tg[3] = {1, 1, 1};
+            ok = wait_flags_geq_cap<kFlagPollNs, 3>(fl, tg, limit, status);
+          }
           if (!ok) return;
           fence_proxy_async_global();
           if (!mbar_wait(&bar_empty[g * kStages + st], (round & 1u) ^ 1u, limit)) {
@@ -385,11 +392,23 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
           last_parity[g][st] = round & 1u;
         });
         if (finisher && ok) {
-          if (D >= 1)
-            ok = wait_flag<I64>(a.flags + tile_index(inst, I, I), 1, limit, status) &&
-                 wait_flag<I64>(a.flags + tile_index(inst, J, J), 1, limit, status) &&
-                 wait_flag<I64>(a.flags + tile_index(inst, I + 1, J), 1, limit, status);
-          if (ok && task.nparts > 0) ok = wait_flag<I64>(a.counters + tidx, task.nparts, limit, status);
+          if constexpr (I64) {
+            if (D >= 1)
+              ok = wait_flag<I64>(a.flags + tile_index(inst, I, I), 1, limit, status) &&
+                   wait_flag<I64>(a.flags + tile_index(inst, J, J), 1, limit, status) &&
+                   wait_flag<I64>(a.flags + tile_index(inst, I + 1, J), 1, limit, status);
+            if (ok && task.nparts > 0) ok = wait_flag<I64>(a.counters + tidx, task.nparts, limit, status);
+          } else {
+            // tiles (I, I), (J, J), (I+1, J) and the bulk-task counter in one
+            // round trip when they are ready; a diagonal tile has no
+            // neighbours, so its own flag stands in with target 0
+            const bool nb = D >= 1;
+            const int32_t* const fl[4] = {a.flags + (nb ? tile_index(inst, I, I) : tidx),
+                                          a.flags + (nb ? tile_index(inst, J, J) : tidx),
+                                          a.flags + (nb ? tile_index(inst, I + 1, J) : tidx), a.counters + tidx};
+            const int32_t tg[4] = {nb ? 1 : 0, nb ? 1 : 0, nb ? 1 : 0, task.nparts > 0 ? (int32_t)task.nparts : 0};
+            ok = wait_flags_geq_cap<kFlagPollNs, 4>(fl, tg, limit, status);
+          }
           if (ok) {
             fence_proxy_async_global();
             uint32_t bytes = 3 * 128;
