@@ -190,8 +190,7 @@ dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared
           int fin_lo = rmax;  // the finisher keeps the last level (both neighbours)
           if (fin_lo - rmin < kMinBulkLevels) fin_lo = rmin;
           int nparts = 0;
-          for (int r0 = rmin; r0 < fin_lo; r0 += kLevelsPerPart) {
-            const int r1 = std::min(r0 + kLevelsPerPart - 1, fin_lo - 1);
+          auto add_part = [&](int r0, int r1) {
             dpk::McmTask part{};
             part.inst = (int32_t)b;
             part.I = (int16_t)I;
@@ -201,6 +200,18 @@ dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared
             part.kind = 1;
             items.push_back({SortKey{r1 + 1, 1, (int32_t)b, I, J}, part});
             ++nparts;
+          };
+          if (i64) {
+            for (int r0 = rmin; r0 < fin_lo; r0 += kLevelsPerPart)
+              add_part(r0, std::min(r0 + kLevelsPerPart - 1, fin_lo - 1));
+          } else if (fin_lo > rmin) {
+            int r1 = fin_lo - 1;
+            int r0 = std::max(rmin, r1 - dpk::kLastPartLevels + 1);
+            add_part(r0, r1);
+            for (r1 = r0 - 1; r1 >= rmin; r1 = r0 - 1) {
+              r0 = std::max(rmin, r1 - kLevelsPerPart + 1);
+              add_part(r0, r1);
+            }
           }
           if (nparts > 0) sp->accslot[(size_t)tix] = (int32_t)sp->nslots++;
           fin.r_lo = (int16_t)fin_lo;

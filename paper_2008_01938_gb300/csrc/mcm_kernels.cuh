@@ -59,6 +59,12 @@ constexpr int kStages = 2;                             // bulk-copy stages per g
 // kMinBulkLevels bulk levels is not split at all.
 constexpr int kLevelsPerPart = 8;
 constexpr int kMinBulkLevels = 2;
+// int32 plans cut a tile's bulk levels from the top: the part that ends at
+// the last bulk level D-2 -- the part the finisher is likeliest to wait for,
+// since it becomes ready only when tile-diagonal D-2 is complete -- holds
+// kLastPartLevels levels, and kLevelsPerPart-level parts cover the levels
+// below it.
+constexpr int kLastPartLevels = 4;
 
 struct McmInstDev {
   const int32_t* p;   // dims p[0..n] (set by the prologue)
