@@ -66,6 +66,28 @@ def test_host_validation_without_gpu(lib):
     assert lib.interval_dp_solve(one, None, 40, 0, one, one, None, None) == 1
 
 
+def test_host_wrappers_check_buffers_without_gpu(lib):
+    """The host-buffer wrappers refuse tables of the wrong size, dtype or
+    layout before any library call: a page-locked table is written by the
+    kernel in place, so a short one must never reach it."""
+    import numpy as np
+    import torch
+    from paper_2008_01938_gb300 import api
+    p = np.arange(1, 7, dtype=np.int32)  # 5 matrices
+    with pytest.raises(ValueError, match="m must be"):
+        api.mcm_solve_host(p, m=np.empty((4, 4), np.int32))
+    with pytest.raises(ValueError, match="m must be"):
+        api.mcm_solve_host(p, cost="i64", m=np.empty((5, 5), np.int32))
+    with pytest.raises(ValueError, match="s must be"):
+        api.mcm_solve_host(p, m=torch.empty((5, 5), dtype=torch.int32), s=torch.empty((5, 5), dtype=torch.int32))
+    with pytest.raises(ValueError, match="m must be"):
+        api.mcm_solve_host(p, m=torch.empty((5, 10), dtype=torch.int32)[:, ::2])
+    with pytest.raises(TypeError):
+        api.sdp_solve_host(np.zeros(100, np.int32), [3, 1])
+    with pytest.raises(TypeError):
+        api.sdp_solve_host(torch.zeros(100, dtype=torch.float32), [3, 1])
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     from paper_2008_01938_gb300 import native
     monkeypatch.setattr(native, "_lib", None)
