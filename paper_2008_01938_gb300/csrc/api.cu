@@ -600,6 +600,24 @@ dp_status mcm_solve_host(const int32_t* p_host, int32_t n, dp_cost ct, void* m_h
   return rc;
 }
 
+// Test hooks for the (x) = + jump path: the number of chunks sdp_solve would
+// use, and the path itself with a given number of chunks.
+int32_t dp_test_sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k) {
+  DevState* ds = nullptr;
+  if (!a || k < 1 || current_dev(&ds) != DP_OK) return -1;
+  return sdp_jump_chunks(n, a, k, ds->sms);
+}
+
+dp_status dp_test_sdp_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int32_t chunks,
+                           int32_t* status_dev, void* stream) {
+  if (!ST) return fail(DP_EINVAL, "dp_test_sdp_jump: ST is NULL");
+  dp_status rc = sdp_validate(n, a, k, DP_OP_ADD_MOD32);
+  if (rc != DP_OK) return rc;
+  DevState* ds = nullptr;
+  if ((rc = current_dev(&ds)) != DP_OK) return rc;
+  return sdp_add_jump(ST, n, a, k, chunks, status_dev ? status_dev : ds->status, static_cast<cudaStream_t>(stream));
+}
+
 // Test hook: the device address mcm_solve_host would use for a host range
 // (nullptr: the range goes through a device copy).
 void* dp_test_host_range_device_address(const void* ptr, size_t bytes, int writable) {
@@ -744,6 +762,13 @@ dp_status sdp_solve(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, dp_op 
   if (n <= a[0]) return DP_OK;
   DevState* ds = nullptr;
   if ((rc = current_dev(&ds)) != DP_OK) return rc;
+  if (op == DP_OP_ADD_MOD32) {
+    // long tables: chunks from jumped windows, side by side (sdp_jump.cu)
+    const int chunks = sdp_jump_chunks(n, a, k, ds->sms);
+    if (chunks >= 2)
+      return sdp_add_jump(ST, n, a, k, chunks, status_dev ? status_dev : ds->status,
+                          static_cast<cudaStream_t>(stream));
+  }
   dpk::SdpLaunchArgs args{};
   args.insts = nullptr;
   args.one.st = ST;

@@ -79,5 +79,11 @@ dp_status mcm_enqueue(const McmStatic& sp, const McmLayout& L, void* ws, const i
 // ---------------------------------------------------------------------------
 dp_status sdp_validate(int64_t n, const int32_t* a, int32_t k, int op);
 void sdp_shape(int32_t a1, int32_t ak, int* threads, int* ring_log2);
+// (x) = + on one instance, by chunks that start from jumped windows
+// (sdp_jump.cu): the number of chunks the cost model picks (0: solve step by
+// step), and the solve with a given number of chunks.
+int sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k, int sms);
+dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int chunks, int32_t* status,
+                       cudaStream_t st);
 
 }  // namespace dph

@@ -1,0 +1,468 @@
+// sdp_jump.cu -- S-DP with (x) = + modulo 2^32 on one instance, cut into
+// chunks that run side by side.
+//
+// With (x) = +, Eq. (1) is a linear recurrence with constant coefficients
+// over Z/2^32.  Its characteristic polynomial
+//     chi(x) = x^{a_1} - sum_j x^{a_1 - a_j}
+// is monic, so x^N mod chi = sum_{s < a_1} r_s x^s exists over Z/2^32 for
+// every N, and the linear map x^m -> ST[m] vanishes on x^m chi(x) for every
+// m (that is the recurrence).  Hence, for every N and t,
+//     ST[N + t] = sum_{s < a_1} r_s ST[s + t],                          (J)
+// the jump of Fiduccia's method for linear recurrences (C. M. Fiduccia, "An
+// efficient formula for linear recurrences", SIAM J. Comput. 14, 1985): the
+// whole a_1-wide window at N follows from the first 2 a_1 - 1 table values.
+// The paper runs the recurrence one block of cells at a time (Section III);
+// this path gives every chunk of the table its own starting window, so that
+// the chunks run at once on separate SMs:
+//   1. ST[a_1 .. 2 a_1 - 2] by the plain recurrence (the S-DP kernel);
+//   2. g, the impulse response of the recurrence (g[0] = 1, g[m] = sum_j
+//      g[m - a_j]), also by the S-DP kernel;
+//   3. R_1 = x^L mod chi for the chunk length L = L0 2^s (L0 < a_1) by s
+//      squarings of the monomial x^L0, then R_p = x^{pL} mod chi for p < P
+//      by a doubling tree, R_q = R_m R_{q-m} for q in (m, 2m], a level per
+//      round of launches;
+//   4. the windows ST[pL .. pL + a_1 - 1] of all chunks by (J): one batched
+//      Hankel product;
+//   5. the chunks [pL, (p+1)L), one block each, side by side, by the S-DP
+//      kernel, each from its window.
+// Reduction of a product c (degree <= 2 a_1 - 2) modulo chi: let h[d] be the
+// multiple of x^{d - a_1} chi taken away at degree d, from the top down.
+// Then h[d] = c[d] + sum_j h[d + a_j], whose solution is h[d] = sum_m g[m]
+// c[d + m], and the remainder is r[e] = c[e] + sum_j h[e + a_j] over the j
+// with a_1 <= e + a_j <= 2 a_1 - 2.
+// Every product and sum wraps modulo 2^32, which is exact in Z/2^32, so the
+// table is bit-identical to the one the plain recurrence gives.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "api_internal.h"
+#include "sdp_kernels.cuh"
+
+namespace dpk {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Batched Toeplitz product over Z/2^32:
+//   CONV: out[b][t] (+)= sum_s u[b][s] z[b][t - s + zoff]
+//   CORR: out[b][t] (+)= sum_s u[b][s] z[b][t + s + zoff]
+// for t < tout, s < S, z read as 0 outside [0, zlen).  A block computes
+// kTB consecutive outputs over pieces of kSB splits: pieces blockIdx.y,
+// blockIdx.y + gridDim.y, ...  (with gridDim.y > 1 the outputs are added
+// with atomics into a zeroed buffer); blockIdx.z is the batch item.  A thread keeps kTo consecutive outputs and, per inner
+// step of kTs splits, the kTo + kTs - 1 z values they need in registers: 256
+// multiply-adds for 12 shared-memory vector loads.  The staged z window is
+// padded by 4 words every 16, so that the 16-byte loads of a quarter-warp
+// (threads 16 words apart) fall into distinct banks.
+// ---------------------------------------------------------------------------
+constexpr int kTT = 256;                // threads per block
+constexpr int kTo = 16;                 // outputs per thread
+constexpr int kTs = 16;                 // splits per inner step
+constexpr int kTB = kTT * kTo;          // outputs per block
+constexpr int kSB = 512;                // splits per block
+constexpr int kZW = kTB + kSB + 32;     // staged z words
+__host__ __device__ constexpr int zpad(int i) { return i + 4 * (i >> 4); }
+constexpr int kZS = zpad(kZW) + 4;      // padded staging words
+
+struct ToepArgs {
+  const uint32_t* u;
+  int64_t ustride;
+  int64_t S;
+  const uint32_t* z;
+  int64_t zstride;
+  int64_t zlen;
+  int64_t zoff;
+  uint32_t* out;
+  int64_t ostride;
+  int64_t tout;
+  int64_t olim;  // out[b][t] is written only where b * ostride + t < olim
+};
+
+template <bool CONV>
+__global__ void __launch_bounds__(kTT) toeplitz_kernel(const ToepArgs a) {
+  __shared__ __align__(16) uint32_t us[kSB];
+  __shared__ __align__(16) uint32_t zs[kZS];
+  const int tid = threadIdx.x;
+  const int64_t T0 = (int64_t)blockIdx.x * kTB;
+  const int64_t b = blockIdx.z;
+  if (T0 >= a.tout) return;
+  const uint32_t* zb = a.z + b * a.zstride;
+  const uint32_t* ub = a.u + b * a.ustride;
+  uint32_t acc[kTo];
+#pragma unroll
+  for (int q = 0; q < kTo; ++q) acc[q] = 0u;
+  // pieces blockIdx.y, blockIdx.y + gridDim.y, ... of kSB splits each
+  for (int64_t S0 = (int64_t)blockIdx.y * kSB; S0 < a.S; S0 += (int64_t)gridDim.y * kSB) {
+    // z index of output t = T0 + i and split s = S0 + j: c + i - j (CONV) or
+    // c + i + j (CORR); the piece's range of z indices:
+    const int64_t c = CONV ? T0 - S0 + a.zoff : T0 + S0 + a.zoff;
+    const int64_t zmin = CONV ? c - (kSB - 1) : c;
+    const int64_t zmax = CONV ? c + (kTB - 1) : c + (kTB - 1) + (kSB - 1);
+    if (zmax < 0 || zmin >= a.zlen) continue;  // every product of the piece is zero (same for the whole block)
+    // zs[i] holds z[zbase + i]; thread tid at inner step j reads the 32 words
+    // from start(tid, j), a multiple of 16
+    const int64_t zbase = CONV ? c - kSB - 15 : c;
+    __syncthreads();  // the previous piece's reads are done
+    for (int i = tid; i < kZW; i += kTT) {
+      const int64_t zi = zbase + i;
+      zs[zpad(i)] = (zi >= 0 && zi < a.zlen) ? zb[zi] : 0u;
+    }
+    for (int i = tid; i < kSB; i += kTT) us[i] = S0 + i < a.S ? ub[S0 + i] : 0u;
+    __syncthreads();
+#pragma unroll 1
+    for (int j = 0; j < kSB; j += kTs) {
+      uint32_t ur[kTs], zr[32];
+#pragma unroll
+      for (int v = 0; v < kTs / 4; ++v) {
+        const uint4 x = *reinterpret_cast<const uint4*>(us + j + 4 * v);
+        ur[4 * v] = x.x;
+        ur[4 * v + 1] = x.y;
+        ur[4 * v + 2] = x.z;
+        ur[4 * v + 3] = x.w;
+      }
+      const int start = CONV ? kTo * tid - j + kSB : kTo * tid + j;
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const uint4 x = *reinterpret_cast<const uint4*>(zs + zpad(start + 4 * v));
+        zr[4 * v] = x.x;
+        zr[4 * v + 1] = x.y;
+        zr[4 * v + 2] = x.z;
+        zr[4 * v + 3] = x.w;
+      }
+      // CONV: z index c + kTo*tid + q - (j + r) = zbase + start + 15 + q - r
+      // CORR: z index c + kTo*tid + q + (j + r) = zbase + start + q + r
+#pragma unroll
+      for (int r = 0; r < kTs; ++r)
+#pragma unroll
+        for (int q = 0; q < kTo; ++q) acc[q] += ur[r] * zr[CONV ? 15 + q - r : q + r];
+    }
+  }
+  // every output of the block is written (zero where no piece contributed);
+  // with the split range divided between blocks (gridDim.y > 1) the pieces'
+  // sums are added into a zeroed buffer
+  uint32_t* ob = a.out + b * a.ostride;
+  const bool split = gridDim.y > 1;
+#pragma unroll
+  for (int q = 0; q < kTo; ++q) {
+    const int64_t t = T0 + (int64_t)kTo * tid + q;
+    if (t < a.tout && b * a.ostride + t < a.olim) {
+      if (split)
+        atomicAdd(ob + t, acc[q]);
+      else
+        ob[t] = acc[q];
+    }
+  }
+}
+
+// r[b][e] = c[b][e] + sum_j h[b][e + a_j - A] over the j with A <= e + a_j <=
+// 2A - 2, for e < A: the remainder of the reduction modulo chi.
+__global__ void __launch_bounds__(256) fold_kernel(const uint32_t* c, int64_t cstride, const uint32_t* h,
+                                                   int64_t hstride, uint32_t* r, int64_t rstride,
+                                                   const int32_t* offs, int k, int A) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t b = blockIdx.y;
+  if (e >= A) return;
+  uint32_t v = c[b * cstride + e];
+  const uint32_t* hb = h + b * hstride;
+  for (int j = 0; j < k; ++j) {
+    const int d = e + offs[j];
+    if (d >= A && d <= 2 * A - 2) v += hb[d - A];
+  }
+  r[b * rstride + e] = v;
+}
+
+struct JumpSetup {
+  int32_t offs[kSdpMaxK];
+  int32_t k;
+  int32_t A;
+  int32_t L0;
+  int32_t P;
+  int64_t L;
+  int64_t n;
+  uint32_t* st;
+  int32_t* d_offs;
+  uint32_t* hbuf;  // 2A - 2 words: preset of the impulse response
+  uint32_t* R1;    // A words: x^L0
+  SdpInstDev* insts;
+};
+
+// Device-side set-up: the offsets, the impulse-response preset (a single 1
+// at position A - 1), the monomial x^L0 and the chunk records.
+__global__ void __launch_bounds__(256) jump_setup_kernel(const JumpSetup s) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < s.k) s.d_offs[i] = s.offs[i];
+  if (i < 2 * (int64_t)s.A - 2) s.hbuf[i] = i == s.A - 1 ? 1u : 0u;
+  if (i < s.A) s.R1[i] = i == s.L0 ? 1u : 0u;
+  if (i < s.P) {
+    SdpInstDev in{};
+    in.st = s.st + i * s.L;
+    in.n = s.n - i * s.L < s.L ? s.n - i * s.L : s.L;
+    in.a = s.d_offs;
+    in.k = s.k;
+    in.a_off = 0;
+    s.insts[i] = in;
+  }
+}
+
+cudaError_t toeplitz(bool conv, const ToepArgs& a, int64_t batch, int sblocks, cudaStream_t st) {
+  const dim3 grid((unsigned)((a.tout + kTB - 1) / kTB), (unsigned)sblocks, (unsigned)batch);
+  if (conv)
+    toeplitz_kernel<true><<<grid, kTT, 0, st>>>(a);
+  else
+    toeplitz_kernel<false><<<grid, kTT, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// s-range pieces for a product of `batch` items with `tblocks` output blocks
+// each: enough blocks to fill the GPU twice over.
+int split_count(int64_t S, int64_t tblocks, int64_t batch, int sms) {
+  const int64_t most = (S + kSB - 1) / kSB;
+  const int64_t want = (2 * (int64_t)sms + tblocks * batch - 1) / (tblocks * batch);
+  return (int)std::max<int64_t>(1, std::min(most, want));
+}
+
+}  // namespace
+}  // namespace dpk
+
+namespace dph {
+
+namespace {
+// Approximate device time of the plain path and of the jump path with P
+// chunks, in microseconds, for the choice between them.  The plain kernel
+// takes about 220 + W (k + 2) / 32 clocks per step of W = min(a_k, 1024)
+// cells (measured at k = 32: 1299 clocks per step); polynomial work runs at
+// an assumed 15 T multiply-adds/s plus about 8 us per launch.
+double plain_us(int64_t cells, int32_t ak, int32_t k) {
+  const double W = std::min<int32_t>(ak, 1024);
+  const double step_us = (220.0 + W * (k + 2) / 32.0) / 2.0e3;
+  return std::ceil((double)cells / W) * step_us;
+}
+
+struct JumpPlan {
+  int P = 0;       // chunks
+  int64_t L = 0;   // chunk length, L0 << s
+  int32_t L0 = 0;  // < a_1
+  int s = 0;       // squarings
+};
+
+// The plan for (about) `chunks` chunks; P = 0 when chunks of at least 2 a_1
+// cells are impossible.
+JumpPlan plan_for(int64_t n, int32_t A, int chunks) {
+  JumpPlan p;
+  if (chunks < 2) return p;
+  const int64_t Lt = (n + chunks - 1) / chunks;
+  if (Lt < 2 * (int64_t)A) return p;
+  int s = 0;
+  while (((Lt + ((int64_t)1 << s) - 1) >> s) >= A) ++s;
+  p.s = s;
+  p.L0 = (int32_t)((Lt + ((int64_t)1 << s) - 1) >> s);
+  p.L = (int64_t)p.L0 << s;
+  p.P = (int)((n + p.L - 1) / p.L);
+  if (p.P < 2) p.P = 0;
+  return p;
+}
+
+double jump_us(int64_t n, int32_t A, int32_t ak, int32_t k, const JumpPlan& p) {
+  const double A2 = (double)A * A;
+  int levels = 0;
+  for (int m = 1; m + 1 <= p.P - 1; m *= 2) ++levels;
+  const double mads = (p.s + std::max(p.P - 2, 0)) * 2.0 * A2 + (p.P - 1) * A2;
+  const double launches = 3.0 * (p.s + levels) + 6.0;
+  return plain_us(std::min<int64_t>(p.L, n) - A, ak, k) + plain_us(2 * (int64_t)A, ak, k) + mads / 15.0e6 +
+         launches * 8.0;
+}
+
+dp_status launch_single(uint32_t* st, int64_t n, const int32_t* a, int32_t k, int op, int32_t* status,
+                        cudaStream_t stream) {
+  dpk::SdpLaunchArgs args{};
+  args.one.st = st;
+  args.one.n = n;
+  args.one.k = k;
+  args.kfull = k == dpk::kSdpMaxKRegs;
+  args.ninst = 1;
+  args.op = op;
+  sdp_shape(a[0], a[k - 1], &args.threads, &args.ring_log2);
+  args.status = status;
+  for (int j = 0; j < k; ++j) args.one_offs[j] = a[j];
+  const cudaError_t e = dpk::launch_sdp(args, stream);
+  return e == cudaSuccess ? DP_OK : fail_cuda(e, "sdp jump: launch of the plain kernel");
+}
+}  // namespace
+
+int sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k, int sms) {
+  const int32_t A = a[0], ak = a[k - 1];
+  if (A < 2 || n < 8 * (int64_t)A) return 0;
+  int32_t tl = 0, rl = 0;
+  sdp_shape(A, ak, &tl, &rl);
+  if (rl <= 0) return 0;  // the chunks need the window on chip
+  const double plain = plain_us(n - A, ak, k);
+  double best = 0.8 * plain;  // the jump must win clearly
+  int bestP = 0;
+  for (int c = 2; c <= sms; ++c) {
+    const JumpPlan p = plan_for(n, A, c);
+    if (p.P < 2) break;
+    const double t = jump_us(n, A, ak, k, p);
+    if (t < best) {
+      best = t;
+      bestP = c;
+    }
+  }
+  return bestP;
+}
+
+dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int chunks, int32_t* status,
+                       cudaStream_t st) {
+  using dpk::ToepArgs;
+  DevState* ds = nullptr;
+  dp_status rc = current_dev(&ds);
+  if (rc != DP_OK) return rc;
+  const int32_t A = a[0];
+  if (A < 2) return fail(DP_EINVAL, "sdp jump: a_1 = %d, the table is constant", A);
+  const JumpPlan pl = plan_for(n, A, chunks);
+  if (pl.P < 2) return fail(DP_EINVAL, "sdp jump: %d chunks of at least %d cells do not fit n = %lld", chunks,
+                            2 * A, (long long)n);
+  int32_t threads = 0, ring_log2 = 0;
+  sdp_shape(A, a[k - 1], &threads, &ring_log2);
+  if (ring_log2 <= 0) return fail(DP_EINVAL, "sdp jump: window a_1 = %d too wide for the on-chip ring", A);
+  const int P = pl.P;
+  // the largest batch of one tree level
+  int64_t nb = 1;
+  for (int64_t m = 1; m + 1 <= P - 1; m *= 2) nb = std::max<int64_t>(nb, std::min<int64_t>(2 * m, P - 1) - m);
+  const int64_t PS = 2 * (int64_t)A;  // product stride (2A - 1 coefficients)
+  const int64_t HS = A;               // stride of the top-down multiples (A - 1 of them)
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  size_t off = 0;
+  const size_t o_offs = off;
+  off += al((size_t)k * 4);
+  const size_t o_h = off;
+  off += al((size_t)(2 * A) * 4);
+  const size_t o_R = off;
+  off += al((size_t)P * A * 4);
+  const size_t o_prod = off;
+  off += al((size_t)nb * PS * 4);
+  const size_t o_hf = off;
+  off += al((size_t)nb * HS * 4);
+  const size_t o_insts = off;
+  off += al((size_t)P * sizeof(dpk::SdpInstDev));
+  uint8_t* ws = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, st);
+  if (e != cudaSuccess) return fail_cuda(e, "sdp jump: workspace");
+  int32_t* d_offs = reinterpret_cast<int32_t*>(ws + o_offs);
+  uint32_t* hbuf = reinterpret_cast<uint32_t*>(ws + o_h);
+  uint32_t* R = reinterpret_cast<uint32_t*>(ws + o_R);
+  uint32_t* prod = reinterpret_cast<uint32_t*>(ws + o_prod);
+  uint32_t* hf = reinterpret_cast<uint32_t*>(ws + o_hf);
+  auto* insts = reinterpret_cast<dpk::SdpInstDev*>(ws + o_insts);
+  const uint32_t* g = hbuf + (A - 1);  // g[m] = hbuf[A - 1 + m]
+
+  const bool prof = profiling();
+  if (prof) profile_mark(1, st, false);
+  auto done = [&](dp_status r) {
+    if (prof) profile_mark(1, st, true);
+    const cudaError_t fe = cudaFreeAsync(ws, st);
+    if (r == DP_OK && fe != cudaSuccess) return fail_cuda(fe, "sdp jump: workspace release");
+    return r;
+  };
+
+  dpk::JumpSetup su{};
+  for (int j = 0; j < k; ++j) su.offs[j] = a[j];
+  su.k = k;
+  su.A = A;
+  su.L0 = pl.L0;
+  su.P = P;
+  su.L = pl.L;
+  su.n = n;
+  su.st = ST;
+  su.d_offs = d_offs;
+  su.hbuf = hbuf;
+  su.R1 = R + A;
+  su.insts = insts;
+  const int64_t su_n = std::max<int64_t>({(int64_t)k, 2 * (int64_t)A, (int64_t)P});
+  dpk::jump_setup_kernel<<<(unsigned)((su_n + 255) / 256), 256, 0, st>>>(su);
+  if ((e = cudaGetLastError()) != cudaSuccess) return done(fail_cuda(e, "sdp jump: set-up"));
+  // 1. ST[A .. 2A - 2]; 2. the impulse response g[0 .. A - 2]
+  if ((rc = launch_single(ST, 2 * (int64_t)A - 1, a, k, DP_OP_ADD_MOD32, status, st)) != DP_OK) return done(rc);
+  if ((rc = launch_single(hbuf, 2 * (int64_t)A - 2, a, k, DP_OP_ADD_MOD32, status, st)) != DP_OK) return done(rc);
+
+  // R[dst + i] = R[x + i * xs] * R[y + i * ys] mod chi for i < cnt
+  auto mulmod = [&](const uint32_t* x, int64_t xs, const uint32_t* y, int64_t ys, uint32_t* dst, int64_t cnt) {
+    const int64_t tb_prod = (2 * (int64_t)A - 1 + dpk::kTB - 1) / dpk::kTB;
+    const int sp = dpk::split_count(A, tb_prod, cnt, ds->sms);
+    if (sp > 1 && (e = cudaMemsetAsync(prod, 0, (size_t)cnt * PS * 4, st)) != cudaSuccess) return e;
+    ToepArgs ta{};
+    ta.u = x;
+    ta.ustride = xs;
+    ta.S = A;
+    ta.z = y;
+    ta.zstride = ys;
+    ta.zlen = A;
+    ta.zoff = 0;
+    ta.out = prod;
+    ta.ostride = PS;
+    ta.tout = 2 * (int64_t)A - 1;
+    ta.olim = INT64_MAX;
+    if ((e = dpk::toeplitz(true, ta, cnt, sp, st)) != cudaSuccess) return e;
+    const int64_t tb_h = (A - 1 + dpk::kTB - 1) / dpk::kTB;
+    const int sh = dpk::split_count(A - 1, tb_h, cnt, ds->sms);
+    if (sh > 1 && (e = cudaMemsetAsync(hf, 0, (size_t)cnt * HS * 4, st)) != cudaSuccess) return e;
+    ToepArgs th{};
+    th.u = g;
+    th.ustride = 0;
+    th.S = A - 1;
+    th.z = prod;
+    th.zstride = PS;
+    th.zlen = 2 * (int64_t)A - 1;
+    th.zoff = A;
+    th.out = hf;
+    th.ostride = HS;
+    th.tout = A - 1;
+    th.olim = INT64_MAX;
+    if ((e = dpk::toeplitz(false, th, cnt, sh, st)) != cudaSuccess) return e;
+    dpk::fold_kernel<<<dim3((unsigned)((A + 255) / 256), (unsigned)cnt), 256, 0, st>>>(prod, PS, hf, HS, dst, A,
+                                                                                       d_offs, k, A);
+    return cudaGetLastError();
+  };
+
+  // 3. R_1 = (x^L0)^(2^s), then R_q = R_m R_{q-m} for q in (m, 2m]
+  for (int i = 0; i < pl.s; ++i)
+    if ((e = mulmod(R + A, 0, R + A, 0, R + A, 1)) != cudaSuccess) return done(fail_cuda(e, "sdp jump: squaring"));
+  for (int64_t m = 1; m + 1 <= P - 1; m *= 2) {
+    const int64_t cnt = std::min<int64_t>(2 * m, P - 1) - m;
+    if ((e = mulmod(R + m * A, 0, R + A, A, R + (m + 1) * A, cnt)) != cudaSuccess)
+      return done(fail_cuda(e, "sdp jump: product tree"));
+  }
+  // 4. windows: ST[pL + t] = sum_s R_p[s] ST[s + t], t < A, for 1 <= p < P
+  {
+    ToepArgs tw{};
+    tw.u = R + A;
+    tw.ustride = A;
+    tw.S = A;
+    tw.z = ST;
+    tw.zstride = 0;
+    tw.zlen = 2 * (int64_t)A - 1;
+    tw.zoff = 0;
+    tw.out = ST + pl.L;
+    tw.ostride = pl.L;
+    tw.tout = A;
+    tw.olim = n - pl.L;
+    if ((e = dpk::toeplitz(false, tw, P - 1, 1, st)) != cudaSuccess) return done(fail_cuda(e, "sdp jump: windows"));
+  }
+  // 5. the chunks, side by side
+  {
+    dpk::SdpLaunchArgs args{};
+    args.insts = insts;
+    args.one.k = k;
+    args.kfull = k == dpk::kSdpMaxKRegs;
+    args.ninst = P;
+    args.op = DP_OP_ADD_MOD32;
+    args.threads = threads;
+    args.ring_log2 = ring_log2;
+    args.status = status;
+    if ((e = dpk::launch_sdp(args, st)) != cudaSuccess) return done(fail_cuda(e, "sdp jump: chunks"));
+  }
+  return done(DP_OK);
+}
+
+}  // namespace dph

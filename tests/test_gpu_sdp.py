@@ -74,6 +74,68 @@ def test_short_tables(dp):
         assert np.array_equal(got, oracle.sdp([3, 1, 4, 1, 5, 9, 2, 6], n, [8, 3], "add"))
 
 
+# (x) = + by chunks from jumped windows (the jump of Fiduccia's method for
+# linear recurrences), forced to a given number of chunks through the test
+# hook: (n, offsets, chunks).  Offsets are a list, or (k, amin, amax, seed)
+# for inputs.sdp_random.
+JUMP_CASES = [
+    (100000, [2, 1], 2),
+    (100003, [2, 1], 152),                  # as many chunks as SMs, ragged tail
+    (50000, [5], 7),                        # one offset: a periodic table
+    (70000, (8, 40, 700, 2), 13),
+    (20000, [9, 8, 7, 6, 5, 4, 3, 2, 1], 9),  # consecutive offsets down to a_k = 1
+    (300000, (32, 1024, 8192, 1), 5),       # the 2^26 workload's offsets: 3 squarings, a tree of 3 products
+    (962, [40, 33, 17, 2], 12),             # last chunk (38 cells) shorter than the window
+    (165, [9, 4, 3], 5),                    # last chunk of 5 cells
+    (400000, (16, 64, 4096, 9), 40),
+]
+
+
+def _jump(dp, preset, n, offsets, chunks):
+    import ctypes
+    import torch
+    from paper_2008_01938_gb300 import native
+    lib = native.load()
+    a = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    st = np.zeros(n, dtype=np.uint32)
+    st[:a[0]] = np.asarray(preset, dtype=np.uint32)[:a[0]]
+    t = torch.from_numpy(st.view(np.int32)).cuda()
+    native.check(lib.dp_test_sdp_jump(ctypes.c_void_p(t.data_ptr()), n, ctypes.c_void_p(a.ctypes.data),
+                                      int(a.size), int(chunks), None, None))
+    dp.sync_status()
+    return t.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("case", JUMP_CASES)
+def test_add_by_jumped_chunks(dp, case):
+    n, offs, chunks = case
+    if isinstance(offs, tuple):
+        k, amin, amax, seed = offs
+        inst = inputs.sdp_random(n=n, k=k, amin=amin, amax=amax, seed=seed)
+        offs, pre = inst.offsets, inst.preset
+    else:
+        pre = inputs.SplitMix64(n + chunks).u32(offs[0])
+    got = _jump(dp, pre, n, offs, chunks)
+    ref = oracle.sdp(pre, n, offs, "add")
+    bad = np.flatnonzero(got != ref)
+    assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5].tolist()}"
+
+
+def test_jump_path_choice_and_refusal(dp):
+    """sdp_solve takes the jump path for the 2^26-cell workload and not for a
+    short table; chunks too short for two windows are refused on the host."""
+    import ctypes
+    from paper_2008_01938_gb300 import native
+    from paper_2008_01938_gb300.native import DpError
+    lib = native.load()
+    big = inputs.sdp_instance_big()
+    a = np.ascontiguousarray(big.offsets.astype(np.int32))
+    assert lib.dp_test_sdp_jump_chunks(big.n, ctypes.c_void_p(a.ctypes.data), int(a.size)) >= 2
+    assert lib.dp_test_sdp_jump_chunks(30000, ctypes.c_void_p(a.ctypes.data), int(a.size)) == 0
+    with pytest.raises(DpError):
+        _jump(dp, big.preset, 40000, big.offsets, 3)   # chunks of 13334 < 2 a_1 cells
+
+
 def fib_pair(i):
     if i == 0:
         return 0, 1
