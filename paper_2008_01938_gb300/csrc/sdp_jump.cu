@@ -61,23 +61,27 @@ constexpr int kTT = 256;                // threads per block
 constexpr int kTo = 16;                 // outputs per thread
 constexpr int kTs = 16;                 // splits per inner step
 constexpr int kTB = kTT * kTo;          // outputs per block
-constexpr int kSB = 512;                // splits per block
+constexpr int kSB = 128;                // splits per piece
 constexpr int kZW = kTB + kSB + 32;     // staged z words
 __host__ __device__ constexpr int zpad(int i) { return i + 4 * (i >> 4); }
 constexpr int kZS = zpad(kZW) + 4;      // padded staging words
 
+// Batch item b is (b_hi, b_lo) = (b / nlo, b % nlo); each operand moves by
+// its lo stride per b_lo and its hi stride per b_hi.
 struct ToepArgs {
   const uint32_t* u;
-  int64_t ustride;
+  int64_t ustride, ustride_hi;
   int64_t S;
   const uint32_t* z;
-  int64_t zstride;
+  int64_t zstride, zstride_hi;
   int64_t zlen;
   int64_t zoff;
+  int64_t zlim;  // z word i of item b is read only where (its offset from z) + i < zlim
   uint32_t* out;
-  int64_t ostride;
+  int64_t ostride, ostride_hi;
   int64_t tout;
-  int64_t olim;  // out[b][t] is written only where b * ostride + t < olim
+  int64_t olim;  // out word t of item b is written only where (its offset from out) + t < olim
+  int64_t nlo;
 };
 
 template <bool CONV>
@@ -86,10 +90,13 @@ __global__ void __launch_bounds__(kTT) toeplitz_kernel(const ToepArgs a) {
   __shared__ __align__(16) uint32_t zs[kZS];
   const int tid = threadIdx.x;
   const int64_t T0 = (int64_t)blockIdx.x * kTB;
-  const int64_t b = blockIdx.z;
+  const int64_t b_hi = blockIdx.z / a.nlo, b_lo = blockIdx.z % a.nlo;
   if (T0 >= a.tout) return;
-  const uint32_t* zb = a.z + b * a.zstride;
-  const uint32_t* ub = a.u + b * a.ustride;
+  const int64_t Tw = T0 + (int64_t)(tid >> 5) * (32 * kTo);  // the warp's first output
+  const int64_t zo = b_hi * a.zstride_hi + b_lo * a.zstride;
+  const uint32_t* zb = a.z + zo;
+  const int64_t zlen = a.zlen < a.zlim - zo ? a.zlen : a.zlim - zo;
+  const uint32_t* ub = a.u + b_hi * a.ustride_hi + b_lo * a.ustride;
   uint32_t acc[kTo];
 #pragma unroll
   for (int q = 0; q < kTo; ++q) acc[q] = 0u;
@@ -100,19 +107,23 @@ __global__ void __launch_bounds__(kTT) toeplitz_kernel(const ToepArgs a) {
     const int64_t c = CONV ? T0 - S0 + a.zoff : T0 + S0 + a.zoff;
     const int64_t zmin = CONV ? c - (kSB - 1) : c;
     const int64_t zmax = CONV ? c + (kTB - 1) : c + (kTB - 1) + (kSB - 1);
-    if (zmax < 0 || zmin >= a.zlen) continue;  // every product of the piece is zero (same for the whole block)
+    if (zmax < 0 || zmin >= zlen) continue;  // every product of the piece is zero (same for the whole block)
     // zs[i] holds z[zbase + i]; thread tid at inner step j reads the 32 words
     // from start(tid, j), a multiple of 16
     const int64_t zbase = CONV ? c - kSB - 15 : c;
     __syncthreads();  // the previous piece's reads are done
     for (int i = tid; i < kZW; i += kTT) {
       const int64_t zi = zbase + i;
-      zs[zpad(i)] = (zi >= 0 && zi < a.zlen) ? zb[zi] : 0u;
+      zs[zpad(i)] = (zi >= 0 && zi < zlen) ? zb[zi] : 0u;
     }
     for (int i = tid; i < kSB; i += kTT) us[i] = S0 + i < a.S ? ub[S0 + i] : 0u;
     __syncthreads();
 #pragma unroll 1
     for (int j = 0; j < kSB; j += kTs) {
+      // the warp's z indices at this step; all outside [0, zlen): nothing to add
+      const int64_t wlo = CONV ? Tw - (S0 + j) - (kTs - 1) + a.zoff : Tw + S0 + j + a.zoff;
+      const int64_t whi = wlo + (32 * kTo - 1) + (kTs - 1);
+      if (whi < 0 || wlo >= zlen) continue;
       uint32_t ur[kTs], zr[32];
 #pragma unroll
       for (int v = 0; v < kTs / 4; ++v) {
@@ -142,12 +153,13 @@ __global__ void __launch_bounds__(kTT) toeplitz_kernel(const ToepArgs a) {
   // every output of the block is written (zero where no piece contributed);
   // with the split range divided between blocks (gridDim.y > 1) the pieces'
   // sums are added into a zeroed buffer
-  uint32_t* ob = a.out + b * a.ostride;
+  const int64_t oo = b_hi * a.ostride_hi + b_lo * a.ostride;
+  uint32_t* ob = a.out + oo;
   const bool split = gridDim.y > 1;
 #pragma unroll
   for (int q = 0; q < kTo; ++q) {
     const int64_t t = T0 + (int64_t)kTo * tid + q;
-    if (t < a.tout && b * a.ostride + t < a.olim) {
+    if (t < a.tout && oo + t < a.olim) {
       if (split)
         atomicAdd(ob + t, acc[q]);
       else
@@ -178,18 +190,22 @@ struct JumpSetup {
   int32_t k;
   int32_t A;
   int32_t L0;
-  int32_t P;
-  int64_t L;
+  int32_t P;    // chunks
+  int32_t P1e;  // major windows, counting the preset's
+  int64_t L;    // chunk length
+  int64_t ML;   // distance between major windows (P2 L)
   int64_t n;
   uint32_t* st;
   int32_t* d_offs;
   uint32_t* hbuf;  // 2A - 2 words: preset of the impulse response
   uint32_t* R1;    // A words: x^L0
-  SdpInstDev* insts;
+  SdpInstDev* insts;      // P chunk records
+  SdpInstDev* ext_insts;  // P1e - 1 records extending major windows 1 .. P1e-1
 };
 
 // Device-side set-up: the offsets, the impulse-response preset (a single 1
-// at position A - 1), the monomial x^L0 and the chunk records.
+// at position A - 1), the monomial x^L0, the chunk records and the records
+// that extend each major window by A - 1 values.
 __global__ void __launch_bounds__(256) jump_setup_kernel(const JumpSetup s) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < s.k) s.d_offs[i] = s.offs[i];
@@ -201,8 +217,16 @@ __global__ void __launch_bounds__(256) jump_setup_kernel(const JumpSetup s) {
     in.n = s.n - i * s.L < s.L ? s.n - i * s.L : s.L;
     in.a = s.d_offs;
     in.k = s.k;
-    in.a_off = 0;
     s.insts[i] = in;
+  }
+  if (i + 1 < s.P1e) {
+    const int64_t pos = (i + 1) * s.ML;
+    SdpInstDev in{};
+    in.st = s.st + pos;
+    in.n = s.n - pos < 2 * (int64_t)s.A - 1 ? s.n - pos : 2 * (int64_t)s.A - 1;
+    in.a = s.d_offs;
+    in.k = s.k;
+    s.ext_insts[i] = in;
   }
 }
 
@@ -215,8 +239,8 @@ cudaError_t toeplitz(bool conv, const ToepArgs& a, int64_t batch, int sblocks, c
   return cudaGetLastError();
 }
 
-// s-range pieces for a product of `batch` items with `tblocks` output blocks
-// each: enough blocks to fill the GPU twice over.
+// split-range pieces for a product of `batch` items with `tblocks` output
+// blocks each: enough blocks to fill the GPU twice over.
 int split_count(int64_t S, int64_t tblocks, int64_t batch, int sms) {
   const int64_t most = (S + kSB - 1) / kSB;
   const int64_t want = (2 * (int64_t)sms + tblocks * batch - 1) / (tblocks * batch);
@@ -229,29 +253,42 @@ int split_count(int64_t S, int64_t tblocks, int64_t batch, int sms) {
 namespace dph {
 
 namespace {
-// Approximate device time of the plain path and of the jump path with P
-// chunks, in microseconds, for the choice between them.  The plain kernel
-// takes about 220 + W (k + 2) / 32 clocks per step of W = min(a_k, 1024)
-// cells (measured at k = 32: 1299 clocks per step); polynomial work runs at
-// an assumed 15 T multiply-adds/s plus about 8 us per launch.
+// Approximate device times, in microseconds, for the choice between the
+// plain path and the jump path.  The plain kernel takes about 220 + W (k +
+// 2) / 32 clocks per step of W = min(a_k, 1024) cells (measured at k = 32:
+// 1299 clocks per step).  A Toeplitz product runs at about 14 T
+// multiply-adds/s (measured); a product modulo chi costs about 1.7 a_1^2 of
+// them in three launches, a window a_1^2, and a round of launches on small
+// batches about 20 us.
 double plain_us(int64_t cells, int32_t ak, int32_t k) {
+  if (cells <= 0) return 0.0;
   const double W = std::min<int32_t>(ak, 1024);
   const double step_us = (220.0 + W * (k + 2) / 32.0) / 2.0e3;
   return std::ceil((double)cells / W) * step_us;
 }
 
+int ceil_log2(int64_t x) {
+  int l = 0;
+  while (((int64_t)1 << l) < x) ++l;
+  return l;
+}
+
+// Chunks of length L = L0 2^s (L0 < A, so x^L0 needs no reduction), P of
+// them, in P1 groups of P2: the windows at multiples of P2 L ("major") come
+// from the preset, the others from the nearest major window.
 struct JumpPlan {
-  int P = 0;       // chunks
-  int64_t L = 0;   // chunk length, L0 << s
-  int32_t L0 = 0;  // < a_1
-  int s = 0;       // squarings
+  int P = 0;
+  int P1 = 0, P2 = 0, P1e = 0;
+  int64_t L = 0;
+  int32_t L0 = 0;
+  int s = 0;
 };
 
-// The plan for (about) `chunks` chunks; P = 0 when chunks of at least 2 a_1
+// The plan for about `chunks` chunks; P = 0 when chunks of at least 2 A
 // cells are impossible.
 JumpPlan plan_for(int64_t n, int32_t A, int chunks) {
   JumpPlan p;
-  if (chunks < 2) return p;
+  if (chunks < 2 || A < 2) return p;
   const int64_t Lt = (n + chunks - 1) / chunks;
   if (Lt < 2 * (int64_t)A) return p;
   int s = 0;
@@ -260,21 +297,26 @@ JumpPlan plan_for(int64_t n, int32_t A, int chunks) {
   p.L0 = (int32_t)((Lt + ((int64_t)1 << s) - 1) >> s);
   p.L = (int64_t)p.L0 << s;
   p.P = (int)((n + p.L - 1) / p.L);
-  if (p.P < 2) p.P = 0;
+  if (p.P < 2) {
+    p.P = 0;
+    return p;
+  }
+  p.P2 = std::max(1, (int)std::lround(std::sqrt((double)p.P)));
+  p.P1 = (p.P + p.P2 - 1) / p.P2;
+  p.P1e = (int)((n + (int64_t)p.P2 * p.L - 1) / ((int64_t)p.P2 * p.L));
   return p;
 }
 
 double jump_us(int64_t n, int32_t A, int32_t ak, int32_t k, const JumpPlan& p) {
   const double A2 = (double)A * A;
-  int levels = 0;
-  for (int m = 1; m + 1 <= p.P - 1; m *= 2) ++levels;
-  const double mads = (p.s + std::max(p.P - 2, 0)) * 2.0 * A2 + (p.P - 1) * A2;
-  const double launches = 3.0 * (p.s + levels) + 6.0;
-  return plain_us(std::min<int64_t>(p.L, n) - A, ak, k) + plain_us(2 * (int64_t)A, ak, k) + mads / 15.0e6 +
-         launches * 8.0;
+  const int products = p.s + (p.P2 - 1) + std::max(p.P1e - 2, 0);
+  const int rounds = p.s + ceil_log2(p.P2) + ceil_log2(std::max(p.P1e - 1, 1)) + 4;
+  const double mads = products * 1.7 * A2 + (p.P - 1) * A2;
+  return plain_us(std::min<int64_t>(p.L, n) - A, ak, k) + 3.0 * plain_us(A, ak, k) + mads / 14.0e6 +
+         rounds * 20.0;
 }
 
-dp_status launch_single(uint32_t* st, int64_t n, const int32_t* a, int32_t k, int op, int32_t* status,
+dp_status launch_single(uint32_t* st, int64_t n, const int32_t* a, int32_t k, int32_t* status,
                         cudaStream_t stream) {
   dpk::SdpLaunchArgs args{};
   args.one.st = st;
@@ -282,12 +324,28 @@ dp_status launch_single(uint32_t* st, int64_t n, const int32_t* a, int32_t k, in
   args.one.k = k;
   args.kfull = k == dpk::kSdpMaxKRegs;
   args.ninst = 1;
-  args.op = op;
+  args.op = DP_OP_ADD_MOD32;
   sdp_shape(a[0], a[k - 1], &args.threads, &args.ring_log2);
   args.status = status;
   for (int j = 0; j < k; ++j) args.one_offs[j] = a[j];
   const cudaError_t e = dpk::launch_sdp(args, stream);
   return e == cudaSuccess ? DP_OK : fail_cuda(e, "sdp jump: launch of the plain kernel");
+}
+
+dp_status launch_records(const dpk::SdpInstDev* insts, int count, int32_t k, int32_t threads, int32_t ring_log2,
+                         int32_t* status, cudaStream_t stream) {
+  if (count <= 0) return DP_OK;
+  dpk::SdpLaunchArgs args{};
+  args.insts = insts;
+  args.one.k = k;
+  args.kfull = k == dpk::kSdpMaxKRegs;
+  args.ninst = count;
+  args.op = DP_OP_ADD_MOD32;
+  args.threads = threads;
+  args.ring_log2 = ring_log2;
+  args.status = status;
+  const cudaError_t e = dpk::launch_sdp(args, stream);
+  return e == cudaSuccess ? DP_OK : fail_cuda(e, "sdp jump: launch of the chunk kernel");
 }
 }  // namespace
 
@@ -297,8 +355,7 @@ int sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k, int sms) {
   int32_t tl = 0, rl = 0;
   sdp_shape(A, ak, &tl, &rl);
   if (rl <= 0) return 0;  // the chunks need the window on chip
-  const double plain = plain_us(n - A, ak, k);
-  double best = 0.8 * plain;  // the jump must win clearly
+  double best = 0.8 * plain_us(n - A, ak, k);  // the jump must win clearly
   int bestP = 0;
   for (int c = 2; c <= sms; ++c) {
     const JumpPlan p = plan_for(n, A, c);
@@ -321,40 +378,52 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   const int32_t A = a[0];
   if (A < 2) return fail(DP_EINVAL, "sdp jump: a_1 = %d, the table is constant", A);
   const JumpPlan pl = plan_for(n, A, chunks);
-  if (pl.P < 2) return fail(DP_EINVAL, "sdp jump: %d chunks of at least %d cells do not fit n = %lld", chunks,
-                            2 * A, (long long)n);
+  if (pl.P < 2)
+    return fail(DP_EINVAL, "sdp jump: %d chunks of at least %d cells do not fit n = %lld", chunks, 2 * A,
+                (long long)n);
   int32_t threads = 0, ring_log2 = 0;
   sdp_shape(A, a[k - 1], &threads, &ring_log2);
   if (ring_log2 <= 0) return fail(DP_EINVAL, "sdp jump: window a_1 = %d too wide for the on-chip ring", A);
-  const int P = pl.P;
-  // the largest batch of one tree level
-  int64_t nb = 1;
-  for (int64_t m = 1; m + 1 <= P - 1; m *= 2) nb = std::max<int64_t>(nb, std::min<int64_t>(2 * m, P - 1) - m);
+  const int P = pl.P, P2 = pl.P2, P1e = pl.P1e;
+  const int64_t ML = (int64_t)P2 * pl.L;
+  // largest batch of a tree level: R_2 .. R_P2 and Q_2 .. Q_{P1e-1}
+  auto widest = [](int64_t qmax) {
+    int64_t w = 1;
+    for (int64_t m = 1; m + 1 <= qmax; m *= 2) w = std::max<int64_t>(w, std::min<int64_t>(2 * m, qmax) - m);
+    return w;
+  };
+  const int64_t nb = std::max(widest(P2), widest(P1e - 1));
   const int64_t PS = 2 * (int64_t)A;  // product stride (2A - 1 coefficients)
   const int64_t HS = A;               // stride of the top-down multiples (A - 1 of them)
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   size_t off = 0;
-  const size_t o_offs = off;
-  off += al((size_t)k * 4);
-  const size_t o_h = off;
-  off += al((size_t)(2 * A) * 4);
-  const size_t o_R = off;
-  off += al((size_t)P * A * 4);
-  const size_t o_prod = off;
-  off += al((size_t)nb * PS * 4);
-  const size_t o_hf = off;
-  off += al((size_t)nb * HS * 4);
-  const size_t o_insts = off;
-  off += al((size_t)P * sizeof(dpk::SdpInstDev));
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += al(std::max<size_t>(bytes, 16));
+    return o;
+  };
+  const size_t o_offs = take((size_t)k * 4);
+  const size_t o_h = take((size_t)(2 * A) * 4);
+  const size_t o_R = take((size_t)(P2 + 1) * A * 4);                  // R_0 .. R_P2 (R_0 unused)
+  const size_t o_Q = take((size_t)std::max(P1e, 2) * A * 4);          // Q_0 .. Q_{P1e-1} (Q_0 unused)
+  const size_t o_prod = take((size_t)nb * PS * 4);
+  const size_t o_hf = take((size_t)nb * HS * 4);
+  const int64_t nwin = std::max<int64_t>((int64_t)P1e * P2, 2);     // window scratch rows
+  const size_t o_win = take((size_t)nwin * A * 4);
+  const size_t o_insts = take((size_t)P * sizeof(dpk::SdpInstDev));
+  const size_t o_ext = take((size_t)std::max(P1e - 1, 1) * sizeof(dpk::SdpInstDev));
   uint8_t* ws = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, st);
   if (e != cudaSuccess) return fail_cuda(e, "sdp jump: workspace");
   int32_t* d_offs = reinterpret_cast<int32_t*>(ws + o_offs);
   uint32_t* hbuf = reinterpret_cast<uint32_t*>(ws + o_h);
   uint32_t* R = reinterpret_cast<uint32_t*>(ws + o_R);
+  uint32_t* Q = reinterpret_cast<uint32_t*>(ws + o_Q);
   uint32_t* prod = reinterpret_cast<uint32_t*>(ws + o_prod);
   uint32_t* hf = reinterpret_cast<uint32_t*>(ws + o_hf);
+  uint32_t* win = reinterpret_cast<uint32_t*>(ws + o_win);
   auto* insts = reinterpret_cast<dpk::SdpInstDev*>(ws + o_insts);
+  auto* ext_insts = reinterpret_cast<dpk::SdpInstDev*>(ws + o_ext);
   const uint32_t* g = hbuf + (A - 1);  // g[m] = hbuf[A - 1 + m]
 
   const bool prof = profiling();
@@ -372,21 +441,24 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   su.A = A;
   su.L0 = pl.L0;
   su.P = P;
+  su.P1e = P1e;
   su.L = pl.L;
+  su.ML = ML;
   su.n = n;
   su.st = ST;
   su.d_offs = d_offs;
   su.hbuf = hbuf;
   su.R1 = R + A;
   su.insts = insts;
-  const int64_t su_n = std::max<int64_t>({(int64_t)k, 2 * (int64_t)A, (int64_t)P});
+  su.ext_insts = ext_insts;
+  const int64_t su_n = std::max<int64_t>({(int64_t)k, 2 * (int64_t)A, (int64_t)P, (int64_t)P1e});
   dpk::jump_setup_kernel<<<(unsigned)((su_n + 255) / 256), 256, 0, st>>>(su);
   if ((e = cudaGetLastError()) != cudaSuccess) return done(fail_cuda(e, "sdp jump: set-up"));
   // 1. ST[A .. 2A - 2]; 2. the impulse response g[0 .. A - 2]
-  if ((rc = launch_single(ST, 2 * (int64_t)A - 1, a, k, DP_OP_ADD_MOD32, status, st)) != DP_OK) return done(rc);
-  if ((rc = launch_single(hbuf, 2 * (int64_t)A - 2, a, k, DP_OP_ADD_MOD32, status, st)) != DP_OK) return done(rc);
+  if ((rc = launch_single(ST, 2 * (int64_t)A - 1, a, k, status, st)) != DP_OK) return done(rc);
+  if ((rc = launch_single(hbuf, 2 * (int64_t)A - 2, a, k, status, st)) != DP_OK) return done(rc);
 
-  // R[dst + i] = R[x + i * xs] * R[y + i * ys] mod chi for i < cnt
+  // dst + i A = (x + i xs) (y + i ys) mod chi, for i < cnt
   auto mulmod = [&](const uint32_t* x, int64_t xs, const uint32_t* y, int64_t ys, uint32_t* dst, int64_t cnt) {
     const int64_t tb_prod = (2 * (int64_t)A - 1 + dpk::kTB - 1) / dpk::kTB;
     const int sp = dpk::split_count(A, tb_prod, cnt, ds->sms);
@@ -398,70 +470,107 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
     ta.z = y;
     ta.zstride = ys;
     ta.zlen = A;
-    ta.zoff = 0;
+    ta.zlim = INT64_MAX;
     ta.out = prod;
     ta.ostride = PS;
     ta.tout = 2 * (int64_t)A - 1;
     ta.olim = INT64_MAX;
+    ta.nlo = cnt;
     if ((e = dpk::toeplitz(true, ta, cnt, sp, st)) != cudaSuccess) return e;
     const int64_t tb_h = (A - 1 + dpk::kTB - 1) / dpk::kTB;
     const int sh = dpk::split_count(A - 1, tb_h, cnt, ds->sms);
     if (sh > 1 && (e = cudaMemsetAsync(hf, 0, (size_t)cnt * HS * 4, st)) != cudaSuccess) return e;
     ToepArgs th{};
     th.u = g;
-    th.ustride = 0;
     th.S = A - 1;
     th.z = prod;
     th.zstride = PS;
     th.zlen = 2 * (int64_t)A - 1;
     th.zoff = A;
+    th.zlim = INT64_MAX;
     th.out = hf;
     th.ostride = HS;
     th.tout = A - 1;
     th.olim = INT64_MAX;
+    th.nlo = cnt;
     if ((e = dpk::toeplitz(false, th, cnt, sh, st)) != cudaSuccess) return e;
     dpk::fold_kernel<<<dim3((unsigned)((A + 255) / 256), (unsigned)cnt), 256, 0, st>>>(prod, PS, hf, HS, dst, A,
                                                                                        d_offs, k, A);
     return cudaGetLastError();
   };
-
-  // 3. R_1 = (x^L0)^(2^s), then R_q = R_m R_{q-m} for q in (m, 2m]
-  for (int i = 0; i < pl.s; ++i)
-    if ((e = mulmod(R + A, 0, R + A, 0, R + A, 1)) != cudaSuccess) return done(fail_cuda(e, "sdp jump: squaring"));
-  for (int64_t m = 1; m + 1 <= P - 1; m *= 2) {
-    const int64_t cnt = std::min<int64_t>(2 * m, P - 1) - m;
-    if ((e = mulmod(R + m * A, 0, R + A, A, R + (m + 1) * A, cnt)) != cudaSuccess)
-      return done(fail_cuda(e, "sdp jump: product tree"));
-  }
-  // 4. windows: ST[pL + t] = sum_s R_p[s] ST[s + t], t < A, for 1 <= p < P
-  {
+  // X[q] = X[m] X[q - m] for q in (m, 2m], m = 1, 2, 4, ..., up to X[qmax]
+  auto tree = [&](uint32_t* X, int64_t qmax) {
+    for (int64_t m = 1; m + 1 <= qmax; m *= 2) {
+      const int64_t cnt = std::min<int64_t>(2 * m, qmax) - m;
+      if ((e = mulmod(X + m * A, 0, X + A, A, X + (m + 1) * A, cnt)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  // Hankel products into the window scratch (rows win + (hi nlo + lo) A):
+  // row (hi, lo), t < A = sum_s U_(hi, lo)[s] ST[hi zs_hi + s + t]
+  auto windows = [&](const uint32_t* U, int64_t us, int64_t us_hi, int64_t zs_hi, int64_t nhi, int64_t nlo) {
+    if (nhi * nlo <= 0) return cudaSuccess;
+    const int64_t tb = (A + dpk::kTB - 1) / dpk::kTB;
+    const int sp = dpk::split_count(A, tb, nhi * nlo, ds->sms);
+    if ((e = cudaMemsetAsync(win, 0, (size_t)nhi * nlo * A * 4, st)) != cudaSuccess) return e;
     ToepArgs tw{};
-    tw.u = R + A;
-    tw.ustride = A;
+    tw.u = U;
+    tw.ustride = us;
+    tw.ustride_hi = us_hi;
     tw.S = A;
     tw.z = ST;
-    tw.zstride = 0;
+    tw.zstride_hi = zs_hi;
     tw.zlen = 2 * (int64_t)A - 1;
-    tw.zoff = 0;
-    tw.out = ST + pl.L;
-    tw.ostride = pl.L;
+    tw.zlim = n;
+    tw.out = win;
+    tw.ostride = A;
+    tw.ostride_hi = nlo * (int64_t)A;
     tw.tout = A;
-    tw.olim = n - pl.L;
-    if ((e = dpk::toeplitz(false, tw, P - 1, 1, st)) != cudaSuccess) return done(fail_cuda(e, "sdp jump: windows"));
+    tw.olim = INT64_MAX;
+    tw.nlo = nlo;
+    // with one piece the kernel stores instead of adding: same result on the zeroed rows
+    return dpk::toeplitz(false, tw, nhi * nlo, sp, st);
+  };
+  // copies `rows` scratch rows, from row r0, to ST + pos0 + r * pitch,
+  // clipped at n
+  auto place = [&](int64_t r0, int64_t pos0, int64_t pitch, int64_t rows) {
+    int64_t full = 0;
+    while (full < rows && pos0 + full * pitch + A <= n) ++full;
+    if (full > 0 &&
+        (e = cudaMemcpy2DAsync(ST + pos0, (size_t)pitch * 4, win + r0 * A, (size_t)A * 4, (size_t)A * 4, (size_t)full,
+                               cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return e;
+    const int64_t pos = pos0 + full * pitch;
+    if (full < rows && pos < n &&
+        (e = cudaMemcpyAsync(ST + pos, win + (r0 + full) * A, (size_t)(n - pos) * 4, cudaMemcpyDeviceToDevice, st)) !=
+            cudaSuccess)
+      return e;
+    return cudaSuccess;
+  };
+
+  // 3. R_1 = (x^L0)^(2^s); R_2 .. R_P2; Q_i = R_P2^i for i < P1e
+  for (int i = 0; i < pl.s; ++i)
+    if ((e = mulmod(R + A, 0, R + A, 0, R + A, 1)) != cudaSuccess) return done(fail_cuda(e, "sdp jump: squaring"));
+  if ((e = tree(R, P2)) != cudaSuccess) return done(fail_cuda(e, "sdp jump: product tree"));
+  if (P1e > 1) {
+    if ((e = cudaMemcpyAsync(Q + A, R + (int64_t)P2 * A, (size_t)A * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+        (e = tree(Q, P1e - 1)) != cudaSuccess)
+      return done(fail_cuda(e, "sdp jump: product tree of the major windows"));
+  }
+  // 4. major windows at i P2 L (1 <= i < P1e), from the preset; each
+  // extended by A - 1 values; then the windows between them, from the
+  // nearest major window: ST[(i P2 + j) L + t] = sum_s R_j[s] ST[i P2 L + s + t]
+  if ((e = windows(Q + A, A, 0, 0, 1, P1e - 1)) != cudaSuccess || (e = place(0, ML, ML, P1e - 1)) != cudaSuccess)
+    return done(fail_cuda(e, "sdp jump: major windows"));
+  if ((rc = launch_records(ext_insts, P1e - 1, k, threads, ring_log2, status, st)) != DP_OK) return done(rc);
+  if (P2 > 1) {
+    if ((e = windows(R + A, A, 0, ML, P1e, P2 - 1)) != cudaSuccess) return done(fail_cuda(e, "sdp jump: windows"));
+    for (int64_t i = 0; i < P1e; ++i)
+      if ((e = place(i * (P2 - 1), i * ML + pl.L, pl.L, P2 - 1)) != cudaSuccess)
+        return done(fail_cuda(e, "sdp jump: windows"));
   }
   // 5. the chunks, side by side
-  {
-    dpk::SdpLaunchArgs args{};
-    args.insts = insts;
-    args.one.k = k;
-    args.kfull = k == dpk::kSdpMaxKRegs;
-    args.ninst = P;
-    args.op = DP_OP_ADD_MOD32;
-    args.threads = threads;
-    args.ring_log2 = ring_log2;
-    args.status = status;
-    if ((e = dpk::launch_sdp(args, st)) != cudaSuccess) return done(fail_cuda(e, "sdp jump: chunks"));
-  }
+  if ((rc = launch_records(insts, P, k, threads, ring_log2, status, st)) != DP_OK) return done(rc);
   return done(DP_OK);
 }
 
