@@ -343,11 +343,19 @@ def bench_sdp(dp, native, lib, dev, args):
         res[op] = {"cells_per_s": cells / (kms / 1e3), "kernel_ms": kms, "wall_ms": wall * 1e3,
                    "roofline": {"bound": "hbm", "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm,
                                 "unit": "GB/s", "frac": bytes_ / (kms / 1e3) / 1e9 / hbm,
-                                "note": "dependency chain of (n-a_1)/a_k steps bounds it, not HBM"},
-                   "smem_roofline": {"bound": "shared memory of the one SM the chain runs on",
-                                     "achieved": cells * k / (kms / 1e3) / 1e9, "peak": smem_peak,
-                                     "unit": "G words/s", "frac": cells * k / (kms / 1e3) / 1e9 / smem_peak,
-                                     "per_unit": f"{k} window reads per cell"}}
+                                "note": "dependency chain of (n-a_1)/a_k steps bounds it, not HBM"}}
+        av = np.ascontiguousarray(big.offsets.astype(np.int32))
+        chunks = lib.dp_test_sdp_jump_chunks(big.n, ctypes.c_void_p(av.ctypes.data), int(av.size)) \
+            if op == "add" else 0
+        if chunks >= 2:
+            res[op]["path"] = (f"chunks from jumped windows: {chunks} chunks side by side, their windows from "
+                               "products modulo the characteristic polynomial (time covers the whole path)")
+        else:
+            res[op]["path"] = "step by step on one SM"
+            res[op]["smem_roofline"] = {"bound": "shared memory of the one SM the chain runs on",
+                                        "achieved": cells * k / (kms / 1e3) / 1e9, "peak": smem_peak,
+                                        "unit": "G words/s", "frac": cells * k / (kms / 1e3) / 1e9 / smem_peak,
+                                        "per_unit": f"{k} window reads per cell"}
     # the paper's worst case for its pipeline (Section III-A): 32 consecutive
     # offsets, here 1055 .. 1024 (same W = 1024 cells per step, same k)
     cons = np.arange(1055, 1023, -1, dtype=np.int32)
