@@ -82,6 +82,8 @@ struct ToepArgs {
   int64_t tout;
   int64_t olim;  // out word t of item b is written only where (its offset from out) + t < olim
   int64_t nlo;
+  uint32_t* zero;    // zero[0 .. zero_len) is cleared by the grid, for a later launch
+  int64_t zero_len;
 };
 
 template <bool CONV>
@@ -89,6 +91,11 @@ __global__ void __launch_bounds__(kTT) toeplitz_kernel(const ToepArgs a) {
   __shared__ __align__(16) uint32_t us[kSB];
   __shared__ __align__(16) uint32_t zs[kZS];
   const int tid = threadIdx.x;
+  if (a.zero_len > 0) {
+    const int64_t nthreads = (int64_t)gridDim.x * gridDim.y * gridDim.z * kTT;
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    for (int64_t i = blk * kTT + tid; i < a.zero_len; i += nthreads) a.zero[i] = 0u;
+  }
   const int64_t T0 = (int64_t)blockIdx.x * kTB;
   const int64_t b_hi = blockIdx.z / a.nlo, b_lo = blockIdx.z % a.nlo;
   if (T0 >= a.tout) return;
@@ -169,14 +176,19 @@ __global__ void __launch_bounds__(kTT) toeplitz_kernel(const ToepArgs a) {
 }
 
 // r[b][e] = c[b][e] + sum_j h[b][e + a_j - A] over the j with A <= e + a_j <=
-// 2A - 2, for e < A: the remainder of the reduction modulo chi.
-__global__ void __launch_bounds__(256) fold_kernel(const uint32_t* c, int64_t cstride, const uint32_t* h,
+// 2A - 2, for e < A: the remainder of the reduction modulo chi.  The
+// product c is not read again (its upper half was read by the previous
+// launch), so each thread clears c[b][e] and c[b][e + A] for the next
+// product, which adds into a zeroed buffer.
+__global__ void __launch_bounds__(256) fold_kernel(uint32_t* c, int64_t cstride, const uint32_t* h,
                                                    int64_t hstride, uint32_t* r, int64_t rstride,
                                                    const int32_t* offs, int k, int A) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t b = blockIdx.y;
   if (e >= A) return;
   uint32_t v = c[b * cstride + e];
+  c[b * cstride + e] = 0u;
+  if (e + A < cstride) c[b * cstride + e + A] = 0u;
   const uint32_t* hb = h + b * hstride;
   for (int j = 0; j < k; ++j) {
     const int d = e + offs[j];
@@ -240,10 +252,11 @@ cudaError_t toeplitz(bool conv, const ToepArgs& a, int64_t batch, int sblocks, c
 }
 
 // split-range pieces for a product of `batch` items with `tblocks` output
-// blocks each: enough blocks to fill the GPU twice over.
+// blocks each: about five blocks per SM, the most that are resident at once
+// (registers and shared memory both allow five).
 int split_count(int64_t S, int64_t tblocks, int64_t batch, int sms) {
   const int64_t most = (S + kSB - 1) / kSB;
-  const int64_t want = (2 * (int64_t)sms + tblocks * batch - 1) / (tblocks * batch);
+  const int64_t want = (5 * (int64_t)sms + tblocks * batch - 1) / (tblocks * batch);
   return (int)std::max<int64_t>(1, std::min(most, want));
 }
 
@@ -453,17 +466,21 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   su.ext_insts = ext_insts;
   const int64_t su_n = std::max<int64_t>({(int64_t)k, 2 * (int64_t)A, (int64_t)P, (int64_t)P1e});
   dpk::jump_setup_kernel<<<(unsigned)((su_n + 255) / 256), 256, 0, st>>>(su);
-  if ((e = cudaGetLastError()) != cudaSuccess) return done(fail_cuda(e, "sdp jump: set-up"));
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaMemsetAsync(prod, 0, (size_t)nb * PS * 4, st)) != cudaSuccess)
+    return done(fail_cuda(e, "sdp jump: set-up"));
   // 1. ST[A .. 2A - 2]; 2. the impulse response g[0 .. A - 2]
   if ((rc = launch_single(ST, 2 * (int64_t)A - 1, a, k, status, st)) != DP_OK) return done(rc);
   if ((rc = launch_single(hbuf, 2 * (int64_t)A - 2, a, k, status, st)) != DP_OK) return done(rc);
 
   // dst + i A = (x + i xs) (y + i ys) mod chi, for i < cnt
   auto mulmod = [&](const uint32_t* x, int64_t xs, const uint32_t* y, int64_t ys, uint32_t* dst, int64_t cnt) {
+    // prod is all zero here (set-up, then every fold clears what it read);
+    // the product launch clears hf for the reduction that follows it
     const int64_t tb_prod = (2 * (int64_t)A - 1 + dpk::kTB - 1) / dpk::kTB;
     const int sp = dpk::split_count(A, tb_prod, cnt, ds->sms);
-    if (sp > 1 && (e = cudaMemsetAsync(prod, 0, (size_t)cnt * PS * 4, st)) != cudaSuccess) return e;
     ToepArgs ta{};
+    ta.zero = hf;
+    ta.zero_len = cnt * HS;
     ta.u = x;
     ta.ustride = xs;
     ta.S = A;
@@ -479,7 +496,6 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
     if ((e = dpk::toeplitz(true, ta, cnt, sp, st)) != cudaSuccess) return e;
     const int64_t tb_h = (A - 1 + dpk::kTB - 1) / dpk::kTB;
     const int sh = dpk::split_count(A - 1, tb_h, cnt, ds->sms);
-    if (sh > 1 && (e = cudaMemsetAsync(hf, 0, (size_t)cnt * HS * 4, st)) != cudaSuccess) return e;
     ToepArgs th{};
     th.u = g;
     th.S = A - 1;
