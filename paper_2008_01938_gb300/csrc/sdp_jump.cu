@@ -252,11 +252,12 @@ cudaError_t toeplitz(bool conv, const ToepArgs& a, int64_t batch, int sblocks, c
 }
 
 // split-range pieces for a product of `batch` items with `tblocks` output
-// blocks each: about five blocks per SM, the most that are resident at once
-// (registers and shared memory both allow five).
+// blocks each: as many as keep the launch within one wave of five blocks per
+// SM, the most that are resident at once (registers and shared memory both
+// allow five).
 int split_count(int64_t S, int64_t tblocks, int64_t batch, int sms) {
   const int64_t most = (S + kSB - 1) / kSB;
-  const int64_t want = (5 * (int64_t)sms + tblocks * batch - 1) / (tblocks * batch);
+  const int64_t want = (5 * (int64_t)sms) / (tblocks * batch);
   return (int)std::max<int64_t>(1, std::min(most, want));
 }
 
