@@ -15,14 +15,17 @@
 // this path gives every chunk of the table its own starting window, so that
 // the chunks run at once on separate SMs:
 //   1. ST[a_1 .. 2 a_1 - 2] by the plain recurrence (the S-DP kernel);
-//   2. g, the impulse response of the recurrence (g[0] = 1, g[m] = sum_j
-//      g[m - a_j]), also by the S-DP kernel;
-//   3. R_1 = x^L mod chi for the chunk length L = L0 2^s (L0 < a_1) by s
-//      squarings of the monomial x^L0, then R_p = x^{pL} mod chi for p < P
-//      by a doubling tree, R_q = R_m R_{q-m} for q in (m, 2m], a level per
-//      round of launches;
-//   4. the windows ST[pL .. pL + a_1 - 1] of all chunks by (J): one batched
-//      Hankel product;
+//   2. beside it, g, the impulse response of the recurrence (g[0] = 1,
+//      g[m] = sum_j g[m - a_j]) up to m = Gm, by the same kernel;
+//   3. R_1 = x^L mod chi for the chunk length L = L0 2^s (L0 <= Gm) by s
+//      squarings of x^L0 mod chi, which g gives directly
+//      (jump_start_kernel); R_j = x^{jL} for j <= P2 and Q_i = x^{i P2 L}
+//      for i < P1 by doubling trees, R_q = R_m R_{q-m} for q in (m, 2m], a
+//      level per round of launches;
+//   4. the windows at (i P2 + j) L by (J): the "major" ones (j = 0) from the
+//      preset via Q_i, each extended by a_1 - 1 values with the plain
+//      kernel, then the others from their major window via R_j: batched
+//      Hankel products;
 //   5. the chunks [pL, (p+1)L), one block each, side by side, by the S-DP
 //      kernel, each from its window.
 // Reduction of a product c (degree <= 2 a_1 - 2) modulo chi: let h[d] be the
@@ -201,7 +204,6 @@ struct JumpSetup {
   int32_t offs[kSdpMaxK];
   int32_t k;
   int32_t A;
-  int32_t L0;
   int32_t P;    // chunks
   int32_t P1e;  // major windows, counting the preset's
   int64_t L;    // chunk length
@@ -209,20 +211,28 @@ struct JumpSetup {
   int64_t n;
   uint32_t* st;
   int32_t* d_offs;
-  uint32_t* hbuf;  // 2A - 2 words: preset of the impulse response
-  uint32_t* R1;    // A words: x^L0
+  int64_t hlen;     // A + Gm words: the impulse response g[m] at A - 1 + m
+  uint32_t* hbuf;
   SdpInstDev* insts;      // P chunk records
   SdpInstDev* ext_insts;  // P1e - 1 records extending major windows 1 .. P1e-1
+  SdpInstDev* pre_insts;  // 2 records: ST up to 2A - 2, and the impulse response
 };
 
 // Device-side set-up: the offsets, the impulse-response preset (a single 1
-// at position A - 1), the monomial x^L0, the chunk records and the records
-// that extend each major window by A - 1 values.
+// at position A - 1), the chunk records, the records that extend each major
+// window by A - 1 values, and the two records of the first launch.
 __global__ void __launch_bounds__(256) jump_setup_kernel(const JumpSetup s) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < s.k) s.d_offs[i] = s.offs[i];
-  if (i < 2 * (int64_t)s.A - 2) s.hbuf[i] = i == s.A - 1 ? 1u : 0u;
-  if (i < s.A) s.R1[i] = i == s.L0 ? 1u : 0u;
+  if (i < s.A) s.hbuf[i] = i == s.A - 1 ? 1u : 0u;
+  if (i < 2) {
+    SdpInstDev in{};
+    in.st = i == 0 ? s.st : s.hbuf;
+    in.n = i == 0 ? 2 * (int64_t)s.A - 1 : s.hlen;
+    in.a = s.d_offs;
+    in.k = s.k;
+    s.pre_insts[i] = in;
+  }
   if (i < s.P) {
     SdpInstDev in{};
     in.st = s.st + i * s.L;
@@ -240,6 +250,27 @@ __global__ void __launch_bounds__(256) jump_setup_kernel(const JumpSetup s) {
     in.k = s.k;
     s.ext_insts[i] = in;
   }
+}
+
+// R1 = x^L0 mod chi.  For L0 < A the monomial.  Otherwise, from the
+// impulse response g (g[m] = h[A - 1 + m], computed up to m = L0): reversing
+// x^L0 = Q chi + R1 shows that the reversed quotient is the power series
+// 1 / (1 - sum_j x^{a_j}) = sum_m g[m] x^m cut after degree L0 - A, and then
+// R1[A - 1 - t] = g[M + t] - sum over a_j <= t of g[M + t - a_j], M = L0 - A + 1.
+__global__ void __launch_bounds__(256) jump_start_kernel(uint32_t* R1, const uint32_t* h, const int32_t* offs,
+                                                         int k, int A, int64_t L0) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= A) return;
+  if (L0 < A) {
+    R1[t] = t == L0 ? 1u : 0u;
+    return;
+  }
+  const uint32_t* g = h + (A - 1);
+  const int64_t M = L0 - A + 1;
+  uint32_t v = g[M + t];
+  for (int j = 0; j < k; ++j)
+    if (offs[j] <= t) v -= g[M + t - offs[j]];
+  R1[A - 1 - t] = v;
 }
 
 cudaError_t toeplitz(bool conv, const ToepArgs& a, int64_t batch, int sblocks, cudaStream_t st) {
@@ -294,21 +325,24 @@ struct JumpPlan {
   int P = 0;
   int P1 = 0, P2 = 0, P1e = 0;
   int64_t L = 0;
-  int32_t L0 = 0;
+  int64_t L0 = 0;  // <= Gm: x^L0 mod chi comes from the impulse response
+  int64_t Gm = 0;  // the impulse response is computed for m <= Gm (at least A - 1)
   int s = 0;
 };
 
-// The plan for about `chunks` chunks; P = 0 when chunks of at least 2 A
-// cells are impossible.
-JumpPlan plan_for(int64_t n, int32_t A, int chunks) {
+// The plan for about `chunks` chunks with the impulse response up to Gm;
+// P = 0 when chunks of at least 2 A cells are impossible.
+JumpPlan plan_for(int64_t n, int32_t A, int chunks, int64_t Gm) {
   JumpPlan p;
   if (chunks < 2 || A < 2) return p;
   const int64_t Lt = (n + chunks - 1) / chunks;
   if (Lt < 2 * (int64_t)A) return p;
+  Gm = std::max<int64_t>(Gm, A - 1);
   int s = 0;
-  while (((Lt + ((int64_t)1 << s) - 1) >> s) >= A) ++s;
+  while (((Lt + ((int64_t)1 << s) - 1) >> s) > Gm) ++s;
   p.s = s;
-  p.L0 = (int32_t)((Lt + ((int64_t)1 << s) - 1) >> s);
+  p.Gm = Gm;
+  p.L0 = (Lt + ((int64_t)1 << s) - 1) >> s;
   p.L = (int64_t)p.L0 << s;
   p.P = (int)((n + p.L - 1) / p.L);
   if (p.P < 2) {
@@ -326,24 +360,8 @@ double jump_us(int64_t n, int32_t A, int32_t ak, int32_t k, const JumpPlan& p) {
   const int products = p.s + (p.P2 - 1) + std::max(p.P1e - 2, 0);
   const int rounds = p.s + ceil_log2(p.P2) + ceil_log2(std::max(p.P1e - 1, 1)) + 4;
   const double mads = products * 1.7 * A2 + (p.P - 1) * A2;
-  return plain_us(std::min<int64_t>(p.L, n) - A, ak, k) + 3.0 * plain_us(A, ak, k) + mads / 14.0e6 +
-         rounds * 35.0;
-}
-
-dp_status launch_single(uint32_t* st, int64_t n, const int32_t* a, int32_t k, int32_t* status,
-                        cudaStream_t stream) {
-  dpk::SdpLaunchArgs args{};
-  args.one.st = st;
-  args.one.n = n;
-  args.one.k = k;
-  args.kfull = k == dpk::kSdpMaxKRegs;
-  args.ninst = 1;
-  args.op = DP_OP_ADD_MOD32;
-  sdp_shape(a[0], a[k - 1], &args.threads, &args.ring_log2);
-  args.status = status;
-  for (int j = 0; j < k; ++j) args.one_offs[j] = a[j];
-  const cudaError_t e = dpk::launch_sdp(args, stream);
-  return e == cudaSuccess ? DP_OK : fail_cuda(e, "sdp jump: launch of the plain kernel");
+  return plain_us(std::min<int64_t>(p.L, n) - A, ak, k) + plain_us(A, ak, k) +
+         std::max(plain_us(A, ak, k), plain_us(p.Gm + 1, ak, k)) + mads / 14.0e6 + rounds * 35.0;
 }
 
 dp_status launch_records(const dpk::SdpInstDev* insts, int count, int32_t k, int32_t threads, int32_t ring_log2,
@@ -361,6 +379,22 @@ dp_status launch_records(const dpk::SdpInstDev* insts, int count, int32_t k, int
   const cudaError_t e = dpk::launch_sdp(args, stream);
   return e == cudaSuccess ? DP_OK : fail_cuda(e, "sdp jump: launch of the chunk kernel");
 }
+// How far to compute the impulse response for `chunks` chunks: every
+// doubling of its reach saves one squaring and costs a longer plain run.
+int64_t jump_reach(int64_t n, int32_t A, int32_t ak, int32_t k, int chunks) {
+  int64_t best_gm = A - 1;
+  double best = -1.0;
+  for (int64_t gm : {(int64_t)A - 1, 2 * (int64_t)A, 4 * (int64_t)A, 8 * (int64_t)A, 16 * (int64_t)A}) {
+    const JumpPlan p = plan_for(n, A, chunks, gm);
+    if (p.P < 2) return A - 1;
+    const double t = jump_us(n, A, ak, k, p);
+    if (best < 0.0 || t < best) {
+      best = t;
+      best_gm = gm;
+    }
+  }
+  return best_gm;
+}
 }  // namespace
 
 int sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k, int sms) {
@@ -372,7 +406,7 @@ int sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k, int sms) {
   double best = 0.8 * plain_us(n - A, ak, k);  // the jump must win clearly
   int bestP = 0;
   for (int c = 2; c <= sms; ++c) {
-    const JumpPlan p = plan_for(n, A, c);
+    const JumpPlan p = plan_for(n, A, c, jump_reach(n, A, ak, k, c));
     if (p.P < 2) break;
     const double t = jump_us(n, A, ak, k, p);
     if (t < best) {
@@ -391,7 +425,7 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   if (rc != DP_OK) return rc;
   const int32_t A = a[0];
   if (A < 2) return fail(DP_EINVAL, "sdp jump: a_1 = %d, the table is constant", A);
-  const JumpPlan pl = plan_for(n, A, chunks);
+  const JumpPlan pl = plan_for(n, A, chunks, jump_reach(n, A, a[k - 1], k, chunks));
   if (pl.P < 2)
     return fail(DP_EINVAL, "sdp jump: %d chunks of at least %d cells do not fit n = %lld", chunks, 2 * A,
                 (long long)n);
@@ -417,7 +451,8 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
     return o;
   };
   const size_t o_offs = take((size_t)k * 4);
-  const size_t o_h = take((size_t)(2 * A) * 4);
+  const int64_t hlen = A + pl.Gm;  // the impulse response g[m] at A - 1 + m, m <= Gm
+  const size_t o_h = take((size_t)hlen * 4);
   const size_t o_R = take((size_t)(P2 + 1) * A * 4);                  // R_0 .. R_P2 (R_0 unused)
   const size_t o_Q = take((size_t)std::max(P1e, 2) * A * 4);          // Q_0 .. Q_{P1e-1} (Q_0 unused)
   const size_t o_prod = take((size_t)nb * PS * 4);
@@ -426,6 +461,7 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   const size_t o_win = take((size_t)nwin * A * 4);
   const size_t o_insts = take((size_t)P * sizeof(dpk::SdpInstDev));
   const size_t o_ext = take((size_t)std::max(P1e - 1, 1) * sizeof(dpk::SdpInstDev));
+  const size_t o_pre = take(2 * sizeof(dpk::SdpInstDev));
   uint8_t* ws = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), off, st);
   if (e != cudaSuccess) return fail_cuda(e, "sdp jump: workspace");
@@ -438,6 +474,7 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   uint32_t* win = reinterpret_cast<uint32_t*>(ws + o_win);
   auto* insts = reinterpret_cast<dpk::SdpInstDev*>(ws + o_insts);
   auto* ext_insts = reinterpret_cast<dpk::SdpInstDev*>(ws + o_ext);
+  auto* pre_insts = reinterpret_cast<dpk::SdpInstDev*>(ws + o_pre);
   const uint32_t* g = hbuf + (A - 1);  // g[m] = hbuf[A - 1 + m]
 
   const bool prof = profiling();
@@ -453,7 +490,6 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   for (int j = 0; j < k; ++j) su.offs[j] = a[j];
   su.k = k;
   su.A = A;
-  su.L0 = pl.L0;
   su.P = P;
   su.P1e = P1e;
   su.L = pl.L;
@@ -462,16 +498,19 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   su.st = ST;
   su.d_offs = d_offs;
   su.hbuf = hbuf;
-  su.R1 = R + A;
+  su.hlen = hlen;
   su.insts = insts;
   su.ext_insts = ext_insts;
-  const int64_t su_n = std::max<int64_t>({(int64_t)k, 2 * (int64_t)A, (int64_t)P, (int64_t)P1e});
+  su.pre_insts = pre_insts;
+  const int64_t su_n = std::max<int64_t>({(int64_t)k, (int64_t)A, (int64_t)P, (int64_t)P1e, 2});
   dpk::jump_setup_kernel<<<(unsigned)((su_n + 255) / 256), 256, 0, st>>>(su);
   if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaMemsetAsync(prod, 0, (size_t)nb * PS * 4, st)) != cudaSuccess)
     return done(fail_cuda(e, "sdp jump: set-up"));
-  // 1. ST[A .. 2A - 2]; 2. the impulse response g[0 .. A - 2]
-  if ((rc = launch_single(ST, 2 * (int64_t)A - 1, a, k, status, st)) != DP_OK) return done(rc);
-  if ((rc = launch_single(hbuf, 2 * (int64_t)A - 2, a, k, status, st)) != DP_OK) return done(rc);
+  // 1. ST[A .. 2A - 2] and 2. the impulse response g[0 .. Gm], side by side;
+  // then R_1 starts as x^L0 mod chi
+  if ((rc = launch_records(pre_insts, 2, k, threads, ring_log2, status, st)) != DP_OK) return done(rc);
+  dpk::jump_start_kernel<<<(unsigned)((A + 255) / 256), 256, 0, st>>>(R + A, hbuf, d_offs, k, A, pl.L0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return done(fail_cuda(e, "sdp jump: start"));
 
   // dst + i A = (x + i xs) (y + i ys) mod chi, for i < cnt
   auto mulmod = [&](const uint32_t* x, int64_t xs, const uint32_t* y, int64_t ys, uint32_t* dst, int64_t cnt) {
