@@ -608,6 +608,15 @@ int32_t dp_test_sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k) {
   return sdp_jump_chunks(n, a, k, ds->sms);
 }
 
+// Test hook without a device: the jump plan sdp_solve would take for `sms`
+// SMs (out: P, L, L0, squarings, reach of g, P2, major windows, chunks).
+int32_t dp_test_sdp_jump_plan(int64_t n, const int32_t* a, int32_t k, int32_t sms, int64_t* out) {
+  if (!a || !out || k < 1 || k > dpk::kSdpMaxK || sms < 2) return -1;
+  for (int j = 0; j < k; ++j)
+    if (a[j] < 1 || (j > 0 && a[j] >= a[j - 1])) return -1;
+  return sdp_jump_plan(n, a, k, sms, out);
+}
+
 dp_status dp_test_sdp_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int32_t chunks,
                            int32_t* status_dev, void* stream) {
   if (!ST) return fail(DP_EINVAL, "dp_test_sdp_jump: ST is NULL");

@@ -83,6 +83,9 @@ void sdp_shape(int32_t a1, int32_t ak, int* threads, int* ring_log2);
 // (sdp_jump.cu): the number of chunks the cost model picks (0: solve step by
 // step), and the solve with a given number of chunks.
 int sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k, int sms);
+// The plan behind it (host arithmetic only): P, L, L0, squarings, reach of
+// the impulse response, chunks per major window, major windows, chunks asked.
+int sdp_jump_plan(int64_t n, const int32_t* a, int32_t k, int sms, int64_t out[8]);
 dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int chunks, int32_t* status,
                        cudaStream_t st);
 

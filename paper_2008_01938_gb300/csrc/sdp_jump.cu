@@ -417,6 +417,22 @@ int sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k, int sms) {
   return bestP;
 }
 
+int sdp_jump_plan(int64_t n, const int32_t* a, int32_t k, int sms, int64_t out[8]) {
+  const int chunks = sdp_jump_chunks(n, a, k, sms);
+  for (int i = 0; i < 8; ++i) out[i] = 0;
+  if (chunks < 2) return 0;
+  const JumpPlan p = plan_for(n, a[0], chunks, jump_reach(n, a[0], a[k - 1], k, chunks));
+  out[0] = p.P;
+  out[1] = p.L;
+  out[2] = p.L0;
+  out[3] = p.s;
+  out[4] = p.Gm;
+  out[5] = p.P2;
+  out[6] = p.P1e;
+  out[7] = chunks;
+  return chunks;
+}
+
 dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int chunks, int32_t* status,
                        cudaStream_t st) {
   using dpk::ToepArgs;

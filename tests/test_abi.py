@@ -88,6 +88,38 @@ def test_host_wrappers_check_buffers_without_gpu(lib):
         api.sdp_solve_host(torch.zeros(100, dtype=torch.float32), [3, 1])
 
 
+def _jump_plan(lib, n, offs, sms):
+    import numpy as np
+    lib.dp_test_sdp_jump_plan.restype = ctypes.c_int32
+    lib.dp_test_sdp_jump_plan.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_void_p]
+    a = np.ascontiguousarray(np.asarray(offs, dtype=np.int32))
+    out = np.zeros(8, dtype=np.int64)
+    rc = lib.dp_test_sdp_jump_plan(n, ctypes.c_void_p(a.ctypes.data), int(a.size), sms,
+                                   ctypes.c_void_p(out.ctypes.data))
+    return rc, dict(zip(["P", "L", "L0", "s", "Gm", "P2", "P1e", "chunks"], (int(x) for x in out)))
+
+
+def test_jump_plan_without_gpu(lib):
+    """The plan of the (+) jump path (host arithmetic only): chunks of at
+    least two windows that cover the table, x^L0 within the reach of the
+    impulse response, and major windows that cover every chunk."""
+    from paper_2008_01938_gb300 import inputs
+    big = inputs.sdp_instance_big()
+    for n, offs, sms in [(big.n, big.offsets, 152), (1 << 22, [2, 1], 152), (1 << 24, big.offsets, 152),
+                         (10 ** 7, [900, 700, 64], 40)]:
+        rc, p = _jump_plan(lib, n, offs, sms)
+        A = int(offs[0])
+        assert rc >= 2 and p["chunks"] == rc, (n, rc, p)
+        assert 2 <= p["P"] <= sms and p["L"] >= 2 * A
+        assert (p["P"] - 1) * p["L"] < n <= p["P"] * p["L"]
+        assert p["L"] == p["L0"] << p["s"] and 1 <= p["L0"] <= p["Gm"] and p["Gm"] >= A - 1
+        assert p["P1e"] == -(-n // (p["P2"] * p["L"])) and p["P1e"] * p["P2"] >= p["P"]
+    # a short table keeps the step-by-step path; bad offsets are refused
+    assert _jump_plan(lib, 30000, big.offsets, 152)[0] == 0
+    assert _jump_plan(lib, 1 << 26, [5, 5, 1], 152)[0] == -1
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     from paper_2008_01938_gb300 import native
     monkeypatch.setattr(native, "_lib", None)
