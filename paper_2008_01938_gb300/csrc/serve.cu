@@ -4,10 +4,10 @@
 //   1. retires finished launches (event query), marking their requests done;
 //   2. takes the admitted-but-not-started requests (up to max_batch), groups
 //      them by kind (and cost type / operator) and enqueues one batched launch
-//      per group on the next stream of a small pool, without waiting for the
-//      launches already on the GPU -- so requests that arrive while others run
-//      start as soon as the scheduler sees them and their work overlaps on the
-//      device.
+//      per group on the stream of a small pool with the fewest launches in
+//      flight, without waiting for the launches already on the GPU -- so
+//      requests that arrive while others run start as soon as the scheduler
+//      sees them and their work overlaps on the device.
 // Admission (serve_submit) is by footprint: a request is refused with DP_EBUSY
 // when the in-flight count or the bytes of device tables it would add exceed
 // the configured caps; released requests return their bytes.
@@ -337,12 +337,25 @@ void scheduler(Server* S) {
         groups[g].push_back(r);
       }
       std::vector<Launch*> made;
+      // launches in flight per stream (only this thread changes `running`)
+      std::vector<int> busy(S->streams.size(), 0);
+      for (const Launch* R : S->running) ++busy[R->stream];
       for (int g = 0; g < 4; ++g) {
         if (groups[g].empty()) continue;
         Launch* L = new Launch();
         L->reqs = groups[g];
-        L->stream = S->rr;
-        S->rr = (S->rr + 1) % (int)S->streams.size();
+        // the stream with the fewest launches in flight (ties: round robin),
+        // so that a short launch queues behind a long one only when every
+        // stream is busy
+        const int ns = (int)S->streams.size();
+        int pick = S->rr;
+        for (int i = 1; i < ns; ++i) {
+          const int c = (S->rr + i) % ns;
+          if (busy[c] < busy[pick]) pick = c;
+        }
+        L->stream = pick;
+        ++busy[pick];
+        S->rr = (pick + 1) % ns;
         dp_status rc = g < 2 ? launch_mcm_group(S, groups[g], g == 1, L)
                              : launch_sdp_group(S, groups[g], g == 2 ? DP_OP_MIN : DP_OP_ADD_MOD32, L);
         if (rc == DP_OK && cudaEventCreateWithFlags(&L->ev, cudaEventDisableTiming) == cudaSuccess &&
