@@ -54,11 +54,12 @@ namespace {
 // for t < tout, s < S, z read as 0 outside [0, zlen).  A block computes
 // kTB consecutive outputs over pieces of kSB splits: pieces blockIdx.y,
 // blockIdx.y + gridDim.y, ...  (with gridDim.y > 1 the outputs are added
-// with atomics into a zeroed buffer); blockIdx.z is the batch item.  A thread keeps kTo consecutive outputs and, per inner
-// step of kTs splits, the kTo + kTs - 1 z values they need in registers: 256
-// multiply-adds for 12 shared-memory vector loads.  The staged z window is
-// padded by 4 words every 16, so that the 16-byte loads of a quarter-warp
-// (threads 16 words apart) fall into distinct banks.
+// with atomics into a zeroed buffer); blockIdx.z is the batch item.  A
+// thread keeps kTo consecutive outputs and, per inner step of kTs splits,
+// the kTo + kTs - 1 z values they need in registers: 256 multiply-adds for
+// 12 shared-memory vector loads.  The staged z window is padded by 4 words
+// every 16, so that the 16-byte loads of a quarter-warp (threads 16 words
+// apart) fall into distinct banks.
 // ---------------------------------------------------------------------------
 constexpr int kTT = 256;                // threads per block
 constexpr int kTo = 16;                 // outputs per thread
@@ -318,9 +319,10 @@ int ceil_log2(int64_t x) {
   return l;
 }
 
-// Chunks of length L = L0 2^s (L0 < A, so x^L0 needs no reduction), P of
-// them, in P1 groups of P2: the windows at multiples of P2 L ("major") come
-// from the preset, the others from the nearest major window.
+// Chunks of length L = L0 2^s, P of them, in P1 groups of P2: the windows
+// at multiples of P2 L ("major") come from the preset, the others from the
+// nearest major window.  x^L0 mod chi is read off the impulse response,
+// computed up to Gm >= L0 (a monomial when L0 < A).
 struct JumpPlan {
   int P = 0;
   int P1 = 0, P2 = 0, P1e = 0;
