@@ -181,9 +181,11 @@ dp_status launch_mcm_group(Server* S, const std::vector<Req*>& reqs, bool i64, L
   if ((e = cudaMemsetAsync(d_status, 0, 4, st)) != cudaSuccess) return fail_cuda(e, "serve: status");
   uint8_t* m_all = static_cast<uint8_t*>(block->ptr);
   int16_t* s_all = reinterpret_cast<int16_t*>(m_all + m_bytes);
+  // one resident block per SM: the S-DP blocks of concurrent launches then
+  // still fit beside the MCM ones
   rc = mcm_enqueue(*sp, lay, scratch, reinterpret_cast<int32_t*>(ws + o_dims),
                    reinterpret_cast<int64_t*>(ws + o_poff), reinterpret_cast<int64_t*>(ws + o_toff), m_all, s_all,
-                   d_status, st);
+                   d_status, st, 0, -1, 1);
   if (rc != DP_OK) return rc;
   if ((e = cudaMemcpyAsync(L->status_host, d_status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return fail_cuda(e, "serve: status readback");
