@@ -121,6 +121,24 @@ def test_add_by_jumped_chunks(dp, case):
     assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5].tolist()}"
 
 
+def test_host_entry_point_pinned_jump(dp):
+    """(+) on a page-locked host table long enough for the jump path: its
+    kernels read and write the table in host memory, in place."""
+    import ctypes
+    import torch
+    from paper_2008_01938_gb300 import native
+    big = inputs.sdp_instance_big(n=1 << 22)
+    a = np.ascontiguousarray(big.offsets.astype(np.int32))
+    lib = native.load()
+    assert lib.dp_test_sdp_jump_chunks(big.n, ctypes.c_void_p(a.ctypes.data), int(a.size)) >= 2
+    st = torch.zeros(big.n, dtype=torch.int32).pin_memory()
+    st.numpy().view(np.uint32)[:a[0]] = big.preset
+    dp.sdp_solve_host(st, big.offsets, op="add")
+    ref = oracle.sdp(big.preset, big.n, big.offsets, "add")
+    bad = np.flatnonzero(st.numpy().view(np.uint32) != ref)
+    assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5].tolist()}"
+
+
 def test_jump_path_choice_and_refusal(dp):
     """sdp_solve takes the jump path for the 2^26-cell workload and not for a
     short table; chunks too short for two windows are refused on the host."""
