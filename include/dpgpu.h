@@ -225,7 +225,13 @@ dp_status mcm_plan_destroy(void *plan);
  *           from the table in global memory).
  *   op      DP_OP_MIN or DP_OP_ADD_MOD32.
  * Both operators are commutative and associative, so the result does not
- * depend on the order in which the k terms are combined. */
+ * depend on the order in which the k terms are combined.
+ * With DP_OP_ADD_MOD32 and a table long enough (a cost model decides), the
+ * table is cut into chunks that run side by side, each starting from a
+ * window obtained by products modulo the recurrence's characteristic
+ * polynomial.  That path enqueues a few dozen launches and takes a
+ * workspace of a few MB from the stream-ordered allocator (released on the
+ * same stream).  Its result is bit-identical. */
 dp_status sdp_solve(uint32_t *ST, int64_t n, const int32_t *a, int32_t k, dp_op op,
                     int32_t *status_dev, void *stream);
 
