@@ -19,7 +19,7 @@
  *                     weight plus a per-cell weight w[i][j] (the paper
  *                     presents MCM as one instance of the general technique).
  *
- * Readings where the paper is silent (each is also listed in the design doc):
+ * Readings where the paper is silent:
  *   - indices are 0-based: chain A_0..A_{n-1}, A_i is p[i] x p[i+1];
  *   - f(l, r) of Eq. (2) is l + r + p[i]*p[k+1]*p[j+1] (the textbook cost);
  *   - ties between equal-cost splits go to the smallest k;

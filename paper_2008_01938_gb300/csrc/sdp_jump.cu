@@ -21,7 +21,7 @@
 //      squarings of x^L0 mod chi, which g gives directly
 //      (jump_start_kernel); R_j = x^{jL} for j <= P2 and Q_i = x^{i P2 L}
 //      for i < P1 by doubling trees, R_q = R_m R_{q-m} for q in (m, 2m], a
-//      level per round of launches;
+//      level per set of launches;
 //   4. the windows at (i P2 + j) L by (J): the "major" ones (j = 0) from the
 //      preset via Q_i, each extended by a_1 - 1 values with the plain
 //      kernel, then the others from their major window via R_j: batched
@@ -304,8 +304,8 @@ namespace {
 // 2) / 32 clocks per step of W = min(a_k, 1024) cells (measured at k = 32:
 // 1299 clocks per step).  A Toeplitz product runs at about 14 T
 // multiply-adds/s (measured); a product modulo chi costs about 1.7 a_1^2 of
-// them in three launches, a window a_1^2, and a round of launches on small
-// batches about 35 us (measured: three launches of 16, 13 and 5 us).
+// them in three launches, a window a_1^2, and the three launches of one
+// product level on small batches about 35 us (measured: 16, 13 and 5 us).
 double plain_us(int64_t cells, int32_t ak, int32_t k) {
   if (cells <= 0) return 0.0;
   const double W = std::min<int32_t>(ak, 1024);
@@ -360,10 +360,10 @@ JumpPlan plan_for(int64_t n, int32_t A, int chunks, int64_t Gm) {
 double jump_us(int64_t n, int32_t A, int32_t ak, int32_t k, const JumpPlan& p) {
   const double A2 = (double)A * A;
   const int products = p.s + (p.P2 - 1) + std::max(p.P1e - 2, 0);
-  const int rounds = p.s + ceil_log2(p.P2) + ceil_log2(std::max(p.P1e - 1, 1)) + 4;
+  const int levels = p.s + ceil_log2(p.P2) + ceil_log2(std::max(p.P1e - 1, 1)) + 4;
   const double mads = products * 1.7 * A2 + (p.P - 1) * A2;
   return plain_us(std::min<int64_t>(p.L, n) - A, ak, k) + plain_us(A, ak, k) +
-         std::max(plain_us(A, ak, k), plain_us(p.Gm + 1, ak, k)) + mads / 14.0e6 + rounds * 35.0;
+         std::max(plain_us(A, ak, k), plain_us(p.Gm + 1, ak, k)) + mads / 14.0e6 + levels * 35.0;
 }
 
 dp_status launch_records(const dpk::SdpInstDev* insts, int count, int32_t k, int32_t threads, int32_t ring_log2,
