@@ -11,8 +11,9 @@ Also printed in the same JSON line:
   e2e          the same solve through mcm_solve_host (host buffers; the copy
                of p in and of m and s out are inside the timed region);
   roofline     the MCM kernel's INT32 issue rate against the ALU peak
-               (152 SMs x 128 INT32 lanes/clk x clock; 3 integer ops per
-               split evaluation), from CUDA events around each launch;
+               measured in the same run (SM count x INT32 lanes/clk/SM from
+               the library's throughput probe x max SM clock; 3 integer ops
+               per split evaluation), from CUDA events around each launch;
   cpu_baseline the CPU oracle (single thread) on a bounded sample;
   sdp          the 2^26-cell S-DP table, 32 offsets in [1024, 8192] (seed 2),
                both operators: cells/s and HBM GB/s;
@@ -49,9 +50,6 @@ N_MCM = 4096
 EVALS_4096 = (N_MCM ** 3 - N_MCM) // 6
 METRIC = "MCM split-evals/s (n=4096, batched) vs plain; S-DP cells/s; served p99 latency"
 INT_OPS_PER_EVAL = 3          # weight multiply-add, second add, min
-INT32_LANES_PER_SM_CLK = 128  # 4 SMSPs x 32 lanes of integer issue per clock
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
 
 
 def _rank():
@@ -119,6 +117,41 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
+def measure_int32_peak(lib, native, stream):
+    """The INT32 roofline's denominator, measured on this GPU by the
+    library's throughput probe (dp_measure_int32_rates): SM count from the
+    device, lanes per clock per SM from dependency chains of one instruction
+    kind counted in SM cycles.  The peak is the combined rate of both integer
+    pipes (two-input adds, which the compiler spreads over the ALU and FMA
+    pipes) at the maximum SM clock."""
+    out = (ctypes.c_double * 9)()
+    native.check(lib.dp_measure_int32_rates(out, 9, ctypes.c_void_p(stream.cuda_stream)))
+    rec = {"sms": int(out[6]),
+           "lanes_per_clk_sm": {"add3_alu_pipe": round(out[0], 2), "imad_fma_pipe": round(out[1], 2),
+                                "min3_alu_pipe": round(out[2], 2), "add2_both_pipes": round(out[3], 2),
+                                "add3_imad_interleaved": round(out[4], 2)},
+           "bulk_loop_split_evals_per_clk_sm": round(out[5], 3),
+           "probe_clock_mhz": round(out[7], 1), "max_sm_clock_mhz": out[8]}
+    rec["peak_tops"] = rec["sms"] * out[3] * out[8] * 1e6 / 1e12
+    rec["bulk_loop_ceiling_tops"] = INT_OPS_PER_EVAL * rec["sms"] * out[5] * out[8] * 1e6 / 1e12
+    return rec
+
+
+def _int32_roofline(kernel_ms, evals, probe, clocks=None, name="mcm_main_kernel<int32>"):
+    achieved = INT_OPS_PER_EVAL * evals / (kernel_ms / 1e3) / 1e12
+    lanes = probe["lanes_per_clk_sm"]["add2_both_pipes"]
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(probe["peak_tops"], 3),
+            "unit": "Tops/s (INT32)", "frac": round(achieved / probe["peak_tops"], 4),
+            "kernel": name, "kernel_ms": round(kernel_ms, 4),
+            "peak_basis": (f"measured: {probe['sms']} SMs (device) x {lanes:.1f} INT32 lanes/clk/SM "
+                           f"(two-input add probe, both integer pipes) x {probe['max_sm_clock_mhz']:.0f} MHz "
+                           "(max SM clock)"),
+            "frac_of_bulk_loop_ceiling": round(achieved / probe["bulk_loop_ceiling_tops"], 4)}
+    if clocks and clocks.get("sm_mhz"):
+        roof["frac_at_run_clock"] = round(achieved / (probe["peak_tops"] * clocks["sm_mhz"]
+                                                      / probe["max_sm_clock_mhz"]), 4)
+    return roof
+
 def _kernel_source_sha():
     h = hashlib.sha256()
     for f in ["mcm.cu", "mcm_kernels.cuh", "dp_common.cuh"]:
@@ -209,6 +242,8 @@ def run_gb300(args):
     for _ in range(args.warmup):
         dp.mcm_solve(p, "i32", m, s)
     dp.sync_status()
+    probe = measure_int32_peak(lib, native, stream)
+    args.probe = probe
 
     sampler = ClockSampler(local)
     barrier()
@@ -251,13 +286,16 @@ def run_gb300(args):
                                         ctypes.c_void_p(mh_t.data_ptr()), ctypes.c_void_p(sh_t.data_ptr()), sp))
         e2e_steps = max(3, min(args.steps, 20))
         barrier()
-        t0 = time.perf_counter()
+        e2e_s = 0.0
         for _ in range(e2e_steps):
-            flush.fill_(1)
+            flush.fill_(1)           # L2 flush, finished before the timed call starts
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             native.check(lib.mcm_solve_host(ctypes.c_void_p(ph.data_ptr()), N_MCM, native.DP_COST_I32,
                                             ctypes.c_void_p(mh_t.data_ptr()), ctypes.c_void_p(sh_t.data_ptr()), sp))
+            e2e_s += time.perf_counter() - t0
         barrier()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_s /= e2e_steps
         direct = bool(lib.dp_test_host_range_device_address(ctypes.c_void_p(mh_t.data_ptr()),
                                                            mh_t.numel() * 4, 1))
         e2e_parity = (None if parity is None else
@@ -267,17 +305,12 @@ def run_gb300(args):
                "ms_per_step": e2e_s * 1e3, "parity_sha256_ok": e2e_parity,
                "d2h": ("kernel stores into the pinned host tables" if direct
                        else "copy after the solve"),
-               "note": "includes the 256 MiB L2 flush write per step"}
+               "note": "wall clock of the mcm_solve_host call alone (it returns after the tables are in host "
+                       "memory); the L2 flush before each call is outside the timed region"}
 
-    peak = SM_COUNT * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = INT_OPS_PER_EVAL * EVALS_4096 / (kernel_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s (INT32)",
-            "frac": round(achieved / peak, 4), "traffic": _profile_traffic(),
-            "kernel": "mcm_main_kernel<int32>", "kernel_ms": round(kernel_ms, 4),
-            "peak_basis": "152 SMs x 128 INT32 lanes/clk x 2070 MHz (derived, not measured)"}
-    if clocks.get("sm_mhz"):
-        pk2 = SM_COUNT * INT32_LANES_PER_SM_CLK * clocks["sm_mhz"] * 1e6 / 1e12
-        roof["frac_at_run_clock"] = round(achieved / pk2, 4)
+    roof = _int32_roofline(kernel_ms, EVALS_4096, probe, clocks)
+    roof["traffic"] = _profile_traffic()
+    roof["probe"] = probe
 
     out = {
         "metric": METRIC, "value": value, "unit": "split-evals/s", "n_gpus": world, "steps": args.steps,
@@ -339,7 +372,8 @@ def bench_sdp(dp, native, lib, dev, args):
         cells = big.n - a1
         bytes_ = 4 * cells + 4 * a1
         k = int(big.offsets.size)
-        smem_peak = 32 * SM_MAX_MHZ * 1e6 / 1e9   # one SM: 32 shared-memory words per clock, G words/s
+        # one SM: 32 shared-memory words per clock at the max SM clock, G words/s
+        smem_peak = 32 * args.probe["max_sm_clock_mhz"] * 1e6 / 1e9
         res[op] = {"cells_per_s": cells / (kms / 1e3), "kernel_ms": kms, "wall_ms": wall * 1e3,
                    "roofline": {"bound": "hbm", "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm,
                                 "unit": "GB/s", "frac": bytes_ / (kms / 1e3) / 1e9 / hbm,
@@ -417,14 +451,11 @@ def bench_interval(dp, native, lib, dev, args):
         g = json.load(open(gold)).get("interval_obst_n4096_seed5")
         if g:
             parity = hashlib.sha256(m.cpu().numpy().astype("<i4").tobytes()).hexdigest() == g["m_sha256"]
-    peak = SM_COUNT * INT32_LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = INT_OPS_PER_EVAL * EVALS_4096 / (kernel_ms / 1e3) / 1e12
     return {"workload": "interval DP, optimal-BST shape, 4096 cells (4095 keys), key / gap frequencies "
                         "U[1,4] / U[0,4] seed 5, int32 weights, m and s",
             "split_evals_per_s": EVALS_4096 / (ms / 1e3), "ms_per_solve": ms, "main_kernel_ms": kernel_ms,
             "launches_per_solve": 3,
-            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                         "unit": "Tops/s (INT32)", "frac": round(achieved / peak, 4)},
+            "roofline": _int32_roofline(kernel_ms, EVALS_4096, args.probe, name="mcm_main_kernel<int32, weighted>"),
             "parity_sha256_ok": parity, "l2": "flushed between solves (outside the timed events)"}
 
 
@@ -475,7 +506,7 @@ def bench_batched(dp, native, lib, dev, args):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=st):
         plan.solve(p_all, p_off, tab_off, m_all, s_all, stream=st)
-    reps = 3
+    reps = 10
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()

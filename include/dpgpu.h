@@ -80,6 +80,30 @@ dp_status dp_sync_status(void *stream, int32_t *status_dev);
 dp_status dp_profile_begin(void);
 dp_status dp_profile_end(double *mcm_ms, int64_t *mcm_launches, double *sdp_ms, int64_t *sdp_launches);
 
+/* Measured integer throughput of the current device, the denominator of the
+ * MCM kernel's INT32-ALU roofline (the paper has no counterpart: it is a
+ * measurement utility).  Every SM is kept full of independent dependency
+ * chains of one instruction kind; SM clock cycles are counted around the loop
+ * on the device, so the lane figures do not depend on the clock.  Fills
+ * out[0..8] (host doubles, nout >= 9, else DP_EINVAL):
+ *   out[0]  three-input integer add (ALU pipe), lanes per clock per SM
+ *   out[1]  integer multiply-add (FMA pipe), lanes per clock per SM
+ *   out[2]  three-way unsigned minimum (ALU pipe), lanes per clock per SM
+ *   out[3]  two-input integer add, lanes per clock per SM: the compiler
+ *           spreads these over both integer pipes, so this is the combined
+ *           INT32 rate (the roofline's peak)
+ *   out[4]  three-input adds and multiply-adds interleaved 1:1, lanes per
+ *           clock per SM (the solver's two kinds of split-evaluation
+ *           instruction)
+ *   out[5]  the MCM solver's bulk loop (packed keys on a shared-memory panel,
+ *           nothing waiting), split evaluations per clock per SM
+ *   out[6]  SM count of the device (cudaDevAttrMultiProcessorCount)
+ *   out[7]  SM clock seen during the probes, MHz (cycles / event time)
+ *   out[8]  the device's reported maximum SM clock, MHz
+ * Runs twelve short launches on `stream` (about 30 ms in all) and waits for
+ * them; a 16-byte stream-ordered allocation holds the cycle counts. */
+dp_status dp_measure_int32_rates(double *out, int32_t nout, void *stream);
+
 /* ------------------------------------------------------------------------- */
 /* MCM (Section IV-A, Eq. (2))                                                */
 /* ------------------------------------------------------------------------- */

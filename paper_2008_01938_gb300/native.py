@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "DP_OK", 1: "DP_EINVAL", 2: "DP_ENOMEM", 3: "DP_ECUDA", 4: "D
 
 # Every function declared in include/dpgpu.h (checked by the ABI test).
 HEADER_SYMBOLS = [
-    "dp_last_error", "dp_version", "dp_sync_status", "dp_profile_begin", "dp_profile_end",
+    "dp_last_error", "dp_version", "dp_sync_status", "dp_profile_begin", "dp_profile_end", "dp_measure_int32_rates",
     "mcm_solve", "interval_dp_solve", "mcm_solve_noalloc", "mcm_traceback", "mcm_solve_host", "mcm_plan_create", "mcm_solve_batched",
     "mcm_plan_autotune", "mcm_plan_config", "mcm_plan_destroy",
     "sdp_solve", "sdp_solve_host", "sdp_plan_create", "sdp_solve_batched", "sdp_plan_destroy",
@@ -79,6 +79,7 @@ def load(path: str | None = None):
             "dp_profile_begin": ([], ctypes.c_int),
             "dp_profile_end": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], ctypes.c_int),
+            "dp_measure_int32_rates": ([ctypes.POINTER(ctypes.c_double), i32, vp], ctypes.c_int),
             "mcm_solve": ([vp, i32, ctypes.c_int, vp, vp, vp, vp], ctypes.c_int),
             "mcm_solve_noalloc": ([vp, i32, vp, vp, vp, vp], ctypes.c_int),
             "mcm_traceback": ([vp, i32, vp, vp, vp], ctypes.c_int),
