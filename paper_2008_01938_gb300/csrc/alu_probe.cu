@@ -22,9 +22,10 @@
 //      instruction of the solver's split evaluations
 //   5  the MCM bulk loop: the split evaluations of one 32 x 32 tile against
 //      one k-segment, 4 x 2 cells per thread, operands read from shared
-//      memory exactly as the solver's bulk tasks read them (packed keys,
-//      two candidates per three-way minimum, the chunk merge into 64-bit
-//      keys); reported as split evaluations per clock per SM.  This is the
+//      memory exactly as the solver's bulk tasks read them (packed keys, a
+//      multiply-add and a fused add-and-minimum per candidate, the chunk
+//      merge into 64-bit keys); reported as split evaluations per clock per
+//      SM.  This is the
 //      ceiling of the solver's inner loop when nothing waits.
 #include <cuda_runtime.h>
 
@@ -119,8 +120,10 @@ __global__ void __launch_bounds__(kProbeThreads, kBulkBlocksPerSm)
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
-          acc[r][c] = __vimin3_u32(acc[r][c], P[r][c] * pk0 + av0[r] + bv0[c], P[r][c] * pk1 + av1[r] + bv1[c]);
+        for (int c = 0; c < 2; ++c) {
+          acc[r][c] = __viaddmin_u32(P[r][c] * pk0 + av0[r], bv0[c], acc[r][c]);
+          acc[r][c] = __viaddmin_u32(P[r][c] * pk1 + av1[r], bv1[c], acc[r][c]);
+        }
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)

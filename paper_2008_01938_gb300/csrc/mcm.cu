@@ -215,7 +215,10 @@ __device__ __forceinline__ void seg_i32(const uint32_t* __restrict__ A, const ui
     uint32_t acc[4][2];
 #pragma unroll
     for (int r = 0; r < 4; ++r) acc[r][0] = acc[r][1] = 0xFFFFFFFFu;
-    // two splits per update: one three-way minimum for two candidates
+    // One split evaluation is a multiply-add on the FMA pipe (weight plus the
+    // row-panel key) and a fused add-and-minimum (__viaddmin_u32, one ALU-pipe
+    // instruction) that adds the column-panel key and folds the candidate
+    // into the running minimum: two instructions, one on each integer pipe.
 #pragma unroll
     for (int kk = 0; kk < C; kk += 2) {
       const uint4 a0 = *reinterpret_cast<const uint4*>(A + (c0 + kk) * T + 4 * ty);
@@ -228,8 +231,10 @@ __device__ __forceinline__ void seg_i32(const uint32_t* __restrict__ A, const ui
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
-          acc[r][c] = __vimin3_u32(acc[r][c], P[r][c] * pk0 + av0[r] + bv0[c], P[r][c] * pk1 + av1[r] + bv1[c]);
+        for (int c = 0; c < 2; ++c) {
+          acc[r][c] = __viaddmin_u32(P[r][c] * pk0 + av0[r], bv0[c], acc[r][c]);
+          acc[r][c] = __viaddmin_u32(P[r][c] * pk1 + av1[r], bv1[c], acc[r][c]);
+        }
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -625,6 +630,50 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
             Vec4<E> u4 = lds4(Up + SM::row(lane + T - 2) * SM::UPW + 4 * w);  // t = lane - 1 - e
             E pkc = (E)PKIp[SM::row(lane + T - 2)];
             bar_compute();
+            if constexpr (!I64) {
+              // int32: the operands of step e + 1 (independent of the tile
+              // values) are loaded at the start of step e, so the barrier
+              // after the step does not wait for them, and each candidate is
+              // a multiply-add plus a fused add-and-minimum.
+#pragma unroll 1
+              for (int eb = -(T - 1); eb <= T - 2; eb += 4) {
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4) {
+                  const int e = eb + s4;
+                  if (e <= T - 2) {
+                    if (e <= e_last) {
+                      const int dI = e + T - 1;
+                      const int un = 4 * w + e + 4;
+                      const E Rn = Lp[SM::row(un) * T + lane];
+                      const uint32_t Pn = PKJp[SM::row(un)];
+                      const int tn = lane - 2 - e;
+                      const Vec4<E> u4n = lds4(Up + SM::row(tn) * SM::UPW + 4 * w);
+                      const E pkcn = (E)PKIp[SM::row(tn)];
+                      const E xc = Xc[dI * T + lane];             // column operand X[lane - e][lane]
+                      const Vec4<E> x4 = lds4(Xr + dI * T + 4 * w);  // row operands X[li][li + e]
+#pragma unroll
+                      for (int r = 0; r < 4; ++r) {
+                        const int q = (1 + s4 + r) & 3;
+                        m[r] = __viaddmin_u32(u4.v[r] + wv[r] * pkc, xc, m[r]);
+                        m[r] = __viaddmin_u32(R[q] + wv[r] * (E)P[q], x4.v[r], m[r]);
+                      }
+                      // the lane's cell on diagonal e + 1 is final now
+                      const int rr = c0 - e;
+                      const bool own = (unsigned)rr <= 3u;
+                      E v = sel4(rr, m[0], m[1], m[2], m[3]);
+                      if constexpr (W) v += sel4(rr, wt[0], wt[1], wt[2], wt[3]);
+                      sts_if(own, sXr + (uint32_t)(((dI + 1) * T + 4 * w + rr) * (int)sizeof(E)), v);
+                      sts_if(own, sXc + (uint32_t)(((dI + 1) * T + lane) * (int)sizeof(E)), v);
+                      R[(1 + s4) & 3] = Rn;
+                      P[(1 + s4) & 3] = Pn;
+                      u4 = u4n;
+                      pkc = pkcn;
+                    }
+                    bar_compute();
+                  }
+                }
+              }
+            } else {
 #pragma unroll 1
             for (int eb = -(T - 1); eb <= T - 2; eb += 4) {
 #pragma unroll
@@ -663,6 +712,7 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
                   bar_compute();
                 }
               }
+            }
             }
             // ---------------- panels needed by other tiles, then publish ----------------
             const int64_t nn = n;
