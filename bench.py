@@ -379,11 +379,13 @@ def bench_sdp(dp, native, lib, dev, args):
                                 "unit": "GB/s", "frac": bytes_ / (kms / 1e3) / 1e9 / hbm,
                                 "note": "dependency chain of (n-a_1)/a_k steps bounds it, not HBM"}}
         av = np.ascontiguousarray(big.offsets.astype(np.int32))
-        chunks = lib.dp_test_sdp_jump_chunks(big.n, ctypes.c_void_p(av.ctypes.data), int(av.size)) \
-            if op == "add" else 0
+        hook = lib.dp_test_sdp_jump_chunks if op == "add" else lib.dp_test_sdp_min_jump_chunks
+        chunks = hook(big.n, ctypes.c_void_p(av.ctypes.data), int(av.size))
         if chunks >= 2:
+            algebra = ("products modulo the characteristic polynomial over Z/2^32" if op == "add" else
+                       "Boolean products modulo the characteristic polynomial (bitsets) and range minima")
             res[op]["path"] = (f"chunks from jumped windows: {chunks} chunks side by side, their windows from "
-                               "products modulo the characteristic polynomial (time covers the whole path)")
+                               f"{algebra} (time covers the whole path)")
         else:
             res[op]["path"] = "step by step on one SM"
             res[op]["smem_roofline"] = {"bound": "shared memory of the one SM the chain runs on",
@@ -408,7 +410,10 @@ def bench_sdp(dp, native, lib, dev, args):
     kms = c.value / max(d.value, 1)
     res["consecutive_min"] = {"workload": "same n, k=32 consecutive offsets 1055..1024 (the paper's conflict worst "
                                           "case), preset seed 6", "cells_per_s": (big.n - 1055) / (kms / 1e3),
-                              "kernel_ms": kms}
+                              "kernel_ms": kms,
+                              "path": ("chunks from jumped windows" if lib.dp_test_sdp_min_jump_chunks(
+                                  big.n, ctypes.c_void_p(cons.ctypes.data), int(cons.size)) >= 2
+                                  else "step by step on one SM")}
     return res
 
 

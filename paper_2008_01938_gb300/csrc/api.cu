@@ -608,6 +608,33 @@ int32_t dp_test_sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k) {
   return sdp_jump_chunks(n, a, k, ds->sms);
 }
 
+// Test hooks for the (x) = min jump path: the number of chunks sdp_solve
+// would use, and the path itself with a given number of chunks.
+int32_t dp_test_sdp_min_jump_chunks(int64_t n, const int32_t* a, int32_t k) {
+  DevState* ds = nullptr;
+  if (!a || k < 1 || current_dev(&ds) != DP_OK) return -1;
+  return sdp_min_jump_chunks(n, a, k, ds->sms);
+}
+
+// Test hook without a device: the min jump plan sdp_solve would take for
+// `sms` SMs (out: P, L, L0, squarings, chunks).
+int32_t dp_test_sdp_min_jump_plan(int64_t n, const int32_t* a, int32_t k, int32_t sms, int64_t* out) {
+  if (!a || !out || k < 1 || k > dpk::kSdpMaxK || sms < 2) return -1;
+  for (int j = 0; j < k; ++j)
+    if (a[j] < 1 || (j > 0 && a[j] >= a[j - 1])) return -1;
+  return sdp_min_jump_plan(n, a, k, sms, out);
+}
+
+dp_status dp_test_sdp_min_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int32_t chunks,
+                               int32_t* status_dev, void* stream) {
+  if (!ST) return fail(DP_EINVAL, "dp_test_sdp_min_jump: ST is NULL");
+  dp_status rc = sdp_validate(n, a, k, DP_OP_MIN);
+  if (rc != DP_OK) return rc;
+  DevState* ds = nullptr;
+  if ((rc = current_dev(&ds)) != DP_OK) return rc;
+  return sdp_min_jump(ST, n, a, k, chunks, status_dev ? status_dev : ds->status, static_cast<cudaStream_t>(stream));
+}
+
 // Test hook without a device: the jump plan sdp_solve would take for `sms`
 // SMs (out: P, L, L0, squarings, reach of g, P2, major windows, chunks).
 int32_t dp_test_sdp_jump_plan(int64_t n, const int32_t* a, int32_t k, int32_t sms, int64_t* out) {
@@ -776,6 +803,12 @@ dp_status sdp_solve(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, dp_op 
     const int chunks = sdp_jump_chunks(n, a, k, ds->sms);
     if (chunks >= 2)
       return sdp_add_jump(ST, n, a, k, chunks, status_dev ? status_dev : ds->status,
+                          static_cast<cudaStream_t>(stream));
+  } else {
+    // the same for min, with Boolean products (sdp_minjump.cu)
+    const int chunks = sdp_min_jump_chunks(n, a, k, ds->sms);
+    if (chunks >= 2)
+      return sdp_min_jump(ST, n, a, k, chunks, status_dev ? status_dev : ds->status,
                           static_cast<cudaStream_t>(stream));
   }
   dpk::SdpLaunchArgs args{};

@@ -88,5 +88,16 @@ int sdp_jump_chunks(int64_t n, const int32_t* a, int32_t k, int sms);
 int sdp_jump_plan(int64_t n, const int32_t* a, int32_t k, int sms, int64_t out[8]);
 dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int chunks, int32_t* status,
                        cudaStream_t st);
+// (x) = min on one instance, by chunks whose windows come from Boolean
+// products modulo the characteristic polynomial (sdp_minjump.cu): whether the
+// path applies (a_k >= 32, a_1 <= 8192, a long enough table, the window on
+// chip), the number of chunks the cost model picks (0: solve step by step),
+// and the solve with a given number of chunks.
+bool sdp_min_jump_eligible(int64_t n, const int32_t* a, int32_t k);
+int sdp_min_jump_chunks(int64_t n, const int32_t* a, int32_t k, int sms);
+// The plan behind it (host arithmetic only): P, L, L0, squarings, chunks asked.
+int sdp_min_jump_plan(int64_t n, const int32_t* a, int32_t k, int sms, int64_t out[5]);
+dp_status sdp_min_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int chunks, int32_t* status,
+                       cudaStream_t st);
 
 }  // namespace dph

@@ -95,6 +95,9 @@ def load(path: str | None = None):
             "dp_test_sdp_jump_chunks": ([i64, vp, i32], i32),
             "dp_test_sdp_jump_plan": ([i64, vp, i32, i32, vp], i32),
             "dp_test_sdp_jump": ([vp, i64, vp, i32, i32, vp, vp], ctypes.c_int),
+            "dp_test_sdp_min_jump_chunks": ([i64, vp, i32], i32),
+            "dp_test_sdp_min_jump_plan": ([i64, vp, i32, i32, vp], i32),
+            "dp_test_sdp_min_jump": ([vp, i64, vp, i32, i32, vp, vp], ctypes.c_int),
             "dp_test_mcm_drop_task": ([vp, i32, ctypes.c_int, vp, vp, vp, vp, i32, ctypes.c_longlong], ctypes.c_int),
             "sdp_solve": ([vp, i64, vp, i32, ctypes.c_int, vp, vp], ctypes.c_int),
             "sdp_solve_host": ([vp, i64, vp, i32, ctypes.c_int, vp], ctypes.c_int),

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -118,6 +119,35 @@ def test_jump_plan_without_gpu(lib):
     # a short table keeps the step-by-step path; bad offsets are refused
     assert _jump_plan(lib, 30000, big.offsets, 152)[0] == 0
     assert _jump_plan(lib, 1 << 26, [5, 5, 1], 152)[0] == -1
+
+
+def test_min_jump_plan_without_gpu(lib):
+    """The plan of the (min) jump path (host arithmetic only): chunks of at
+    least two windows that cover the table, L = L0 2^s with C_L0 = {L0} (so
+    L0 < a_1); tables with a_k < 32 or a_1 > 8192 keep the step-by-step
+    path."""
+    import ctypes
+    from paper_2008_01938_gb300 import inputs
+    big = inputs.sdp_instance_big()
+
+    def plan(n, offs, sms):
+        a = np.ascontiguousarray(np.asarray(offs, dtype=np.int32))
+        out = np.zeros(5, dtype=np.int64)
+        rc = lib.dp_test_sdp_min_jump_plan(n, ctypes.c_void_p(a.ctypes.data), int(a.size), sms,
+                                           ctypes.c_void_p(out.ctypes.data))
+        return rc, dict(zip(["P", "L", "L0", "s", "chunks"], out.tolist()))
+
+    for n, offs, sms in [(big.n, big.offsets, 152), (1 << 24, [64, 33], 152), (10 ** 7, [900, 700, 64], 40)]:
+        rc, p = plan(n, offs, sms)
+        A = int(offs[0])
+        assert rc >= 2 and p["chunks"] == rc, (n, rc, p)
+        assert 2 <= p["P"] <= sms and p["L"] >= 2 * A
+        assert (p["P"] - 1) * p["L"] < n <= p["P"] * p["L"]
+        assert p["L"] == p["L0"] << p["s"] and 1 <= p["L0"] < A
+    assert plan(30000, big.offsets, 152)[0] == 0          # too short
+    assert plan(1 << 24, [64, 31], 152)[0] == 0            # a_k < 32
+    assert plan(1 << 26, [9000, 4000], 152)[0] == 0       # a_1 > 8192
+    assert plan(1 << 26, [5, 5, 1], 152)[0] == -1         # not strictly decreasing
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):

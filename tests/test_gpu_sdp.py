@@ -121,6 +121,98 @@ def test_add_by_jumped_chunks(dp, case):
     assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5].tolist()}"
 
 
+# (x) = min by chunks whose windows come from Boolean products modulo the
+# characteristic polynomial (Kitamasa's method over the Boolean semiring),
+# forced to a given number of chunks: (n, offsets, chunks, preset kind).
+# The path needs a_k >= 32 and a_1 <= 8192.  "planted": a large constant
+# with a few small values planted, so that windows are not simply the
+# preset's minimum.
+MIN_JUMP_CASES = [
+    (100000, [64, 33], 2, "random"),
+    (100003, [64, 33], 152, "planted"),              # as many chunks as SMs, ragged tail
+    (50000, [40], 7, "random"),                       # one offset: a periodic table
+    (70000, (8, 40, 700, 2), 13, "planted"),
+    (40000, [40, 39, 38, 37, 36, 35, 34, 33, 32], 9, "planted"),  # consecutive offsets, a_k = 32
+    (300000, (32, 1024, 8192, 1), 5, "planted"),     # the 2^26 workload's offsets
+    (962, [40, 33], 12, "random"),                    # last chunk shorter than the window
+    (400000, (16, 64, 4096, 9), 40, "planted"),      # the serving mix's offset recipe
+    (200000, [1024, 768, 512], 20, "planted"),       # common factor 256: C never fills, many runs
+    (120000, [300, 144, 96], 30, "planted"),          # common factor 12, a_1 not a multiple of 32
+    (500000, [8192, 4096 + 2048 + 32], 20, "planted"),  # common factor 32: 256 runs per set
+]
+
+
+def _min_preset(n, a1, kind, seed):
+    rng = inputs.SplitMix64(seed)
+    if kind == "random":
+        return rng.u32(a1)
+    pre = (rng.u32(a1) | np.uint32(0x80000000))
+    pos = rng.randint(0, a1 - 1, 7)
+    pre[pos] = rng.u32(7) >> np.uint32(4)
+    return pre
+
+
+def _min_jump(dp, preset, n, offsets, chunks):
+    import ctypes
+    import torch
+    from paper_2008_01938_gb300 import native
+    lib = native.load()
+    a = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32))
+    st = np.zeros(n, dtype=np.uint32)
+    st[:a[0]] = np.asarray(preset, dtype=np.uint32)[:a[0]]
+    t = torch.from_numpy(st.view(np.int32)).cuda()
+    native.check(lib.dp_test_sdp_min_jump(ctypes.c_void_p(t.data_ptr()), n, ctypes.c_void_p(a.ctypes.data),
+                                          int(a.size), int(chunks), None, None))
+    dp.sync_status()
+    return t.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("case", MIN_JUMP_CASES)
+def test_min_by_jumped_chunks(dp, case):
+    n, offs, chunks, kind = case
+    if isinstance(offs, tuple):
+        k, amin, amax, seed = offs
+        offs = inputs.sdp_random(n=n, k=k, amin=amin, amax=amax, seed=seed).offsets
+    pre = _min_preset(n, int(offs[0]), kind, n + chunks)
+    got = _min_jump(dp, pre, n, offs, chunks)
+    ref = oracle.sdp(pre, n, offs, "min")
+    bad = np.flatnonzero(got != ref)
+    assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5].tolist()}"
+
+
+def test_min_jump_path_choice_and_refusal(dp):
+    """sdp_solve takes the min jump path for the 2^26-cell workload and not
+    for a short table or a_k < 32; a forced jump outside its range is
+    refused on the host."""
+    import ctypes
+    from paper_2008_01938_gb300 import native
+    from paper_2008_01938_gb300.native import DpError
+    lib = native.load()
+    big = inputs.sdp_instance_big()
+    a = np.ascontiguousarray(big.offsets.astype(np.int32))
+    assert lib.dp_test_sdp_min_jump_chunks(big.n, ctypes.c_void_p(a.ctypes.data), int(a.size)) >= 2
+    assert lib.dp_test_sdp_min_jump_chunks(30000, ctypes.c_void_p(a.ctypes.data), int(a.size)) == 0
+    small_ak = np.ascontiguousarray(np.array([64, 31], dtype=np.int32))
+    assert lib.dp_test_sdp_min_jump_chunks(1 << 22, ctypes.c_void_p(small_ak.ctypes.data), 2) == 0
+    with pytest.raises(DpError):
+        _min_jump(dp, big.preset, 40000, big.offsets, 3)     # chunks of 13334 < 2 a_1 cells
+    with pytest.raises(DpError):
+        _min_jump(dp, [1] * 64, 100000, [64, 31], 4)         # a_k < 32
+
+
+def test_min_planted_2p24(dp):
+    """2^24 cells with the 2^26 workload's offsets and a planted preset (large
+    values with seven small ones), through sdp_solve (the min jump path):
+    every cell against the oracle.  With a uniform preset the table settles
+    at the preset's minimum early; planted minima keep the windows varied."""
+    big = inputs.sdp_instance_big(n=1 << 24)
+    pre = _min_preset(big.n, int(big.offsets[0]), "planted", 24)
+    got = _gpu(dp, pre, big.n, big.offsets, "min")
+    ref = oracle.sdp(pre, big.n, big.offsets, "min")
+    bad = np.flatnonzero(got != ref)
+    assert bad.size == 0, f"{bad.size} cells differ, first {bad[:5].tolist()}"
+
+
 def test_host_entry_point_pinned_jump(dp):
     """(+) on a page-locked host table long enough for the jump path: its
     kernels read and write the table in host memory, in place."""
