@@ -561,11 +561,44 @@ def bench_batched(dp, native, lib, dev, args):
             "autotuned": {"levels_per_bulk_task": tuned[0], "blocks_per_sm": tuned[1]}}
 
 
+SERVE_CLASSES = [("mcm", 16, 64), ("mcm", 64, 256), ("mcm", 256, 1024), ("mcm", 1024, 2049),
+                 ("sdp", 1 << 16, 1 << 20), ("sdp", 1 << 20, (1 << 24) + 1)]
+
+
+def _serve_class(r):
+    for i, (kind, lo, hi) in enumerate(SERVE_CLASSES):
+        if r.kind == kind and lo <= r.n < hi:
+            return i
+    return -1
+
+
+def _class_stats(trace, lat_ms):
+    """p50 / p99 / max latency (ms) per request class: MCM by n, S-DP by n."""
+    import numpy as np
+    out = {}
+    for i, (kind, lo, hi) in enumerate(SERVE_CLASSES):
+        v = np.array([l for r, l in zip(trace, lat_ms) if l is not None and _serve_class(r) == i])
+        if v.size:
+            out[f"{kind} n in [{lo}, {hi - 1}]"] = {"requests": int(v.size), "p50_ms": float(np.percentile(v, 50)),
+                                                     "p99_ms": float(np.percentile(v, 99)), "max_ms": float(v.max())}
+    return out
+
+
 def bench_serve(dp, native, dev, args):
+    """The served Poisson trace through the continuous-batching server, and a
+    plain sequential loop (one solve at a time, in arrival order) over the
+    same trace.  The plain loop's service times are measured on a stratified
+    sample (every `serve_sample`-th request) and the loop is simulated over
+    the whole trace with, for each other request, the measured time of the
+    sampled request of the same kind nearest in log n; its latencies include
+    the queueing that an arrival rate above its throughput causes."""
+    import bisect
     import numpy as np
     import torch
     from paper_2008_01938_gb300 import inputs
+    t_gen = time.perf_counter()
     trace = inputs.serve_trace(rate=args.serve_rate, duration=args.serve_seconds, seed=4)
+    t_gen = time.perf_counter() - t_gen
     if not trace:
         return None
     srv = dp.Server(hbm_cap_bytes=150 << 30, max_inflight=100000, num_streams=4, max_batch=64, device=dev.index)
@@ -577,7 +610,7 @@ def bench_serve(dp, native, dev, args):
         srv.release(tk)
     t_base = srv.now() + 0.01
     outstanding = {}
-    lat = []
+    lat = [None] * len(trace)
     busy = 0
     i = 0
     while i < len(trace) or outstanding:
@@ -588,27 +621,30 @@ def bench_serve(dp, native, dev, args):
             if tk is None:
                 busy += 1
                 break
-            outstanding[tk] = t_base + r.t_arrival
+            outstanding[tk] = i
             i += 1
         for tk in list(outstanding):
             res = srv.poll(tk)
             if res is not None:
                 if res.status != 0:
                     raise RuntimeError(f"request failed with status {res.status}")
-                lat.append(res.t_done - outstanding.pop(tk))
+                j = outstanding.pop(tk)
+                lat[j] = (res.t_done - (t_base + trace[j].t_arrival)) * 1e3
                 srv.release(tk)
         time.sleep(2e-5)
     t_end = srv.now()
     srv.close()
-    lat_ms = np.array(lat) * 1e3
+    lat_ms = np.array([x for x in lat if x is not None])
     served = {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-              "max_ms": float(lat_ms.max()), "requests": len(lat),
-              "throughput_req_s": len(lat) / (t_end - t_base), "busy_retries": busy}
-    # plain sequential solve loop over the same trace (service times measured,
-    # queueing simulated in arrival order)
-    svc = []
-    sub = trace[: min(len(trace), 500)]
-    for r in sub:
+              "max_ms": float(lat_ms.max()), "requests": len(lat_ms),
+              "throughput_req_s": len(lat_ms) / (t_end - t_base), "busy_retries": busy,
+              "by_class": _class_stats(trace, lat)}
+    # plain sequential loop: measured service times on a stratified sample
+    step = max(1, args.serve_sample)
+    sample = list(range(0, len(trace), step))
+    svc = {}
+    for j in sample:
+        r = trace[j]
         t0 = time.perf_counter()
         if r.kind == "mcm":
             pt = torch.from_numpy(r.dims).to(dev)
@@ -619,18 +655,35 @@ def bench_serve(dp, native, dev, args):
             tt = torch.from_numpy(st.view(np.int32)).to(dev)
             dp.sdp_solve(tt, r.offsets, op="min", n=r.n)
         dp.sync_status()
-        svc.append(time.perf_counter() - t0)
+        svc[j] = time.perf_counter() - t0
+    by_kind = {}
+    for j in sample:
+        by_kind.setdefault(trace[j].kind, []).append((math.log(trace[j].n), svc[j]))
+    for k in by_kind:
+        by_kind[k].sort()
+    def service(j):
+        if j in svc:
+            return svc[j]
+        pts = by_kind[trace[j].kind]
+        x = math.log(trace[j].n)
+        q = bisect.bisect_left(pts, (x, -1.0))
+        cand = [pts[c] for c in (q - 1, q) if 0 <= c < len(pts)]
+        return min(cand, key=lambda p: abs(p[0] - x))[1]
     fin, lats = 0.0, []
-    for r, sv in zip(sub, svc):
+    for j, r in enumerate(trace):
         start = max(r.t_arrival, fin)
-        fin = start + sv
-        lats.append(fin - r.t_arrival)
-    lats = np.array(lats) * 1e3
-    plain = {"p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
-             "requests": len(sub), "throughput_req_s": len(sub) / fin if fin > 0 else None}
+        fin = start + service(j)
+        lats.append((fin - r.t_arrival) * 1e3)
+    lats_a = np.array(lats)
+    plain = {"p50_ms": float(np.percentile(lats_a, 50)), "p99_ms": float(np.percentile(lats_a, 99)),
+             "requests": len(trace), "throughput_req_s": len(trace) / fin if fin > 0 else None,
+             "by_class": _class_stats(trace, lats),
+             "method": (f"one solve at a time in arrival order; service times measured on every {step}th request "
+                        f"({len(sample)} solves), the others take the time of the sampled request of the same kind "
+                        "nearest in log n; queueing simulated over the whole trace")}
     return {"workload": f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.0f} s (seed 4): 80% MCM "
                         f"n log-U[16,2048] int64, 20% S-DP n log-U[2^16,2^24] k=16 min; cap 150 GB",
-            "served": served, "plain_sequential_loop": plain}
+            "trace_generation_s": t_gen, "served": served, "plain_sequential_loop": plain}
 
 
 # ---------------------------------------------------------------------------
@@ -674,7 +727,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--extras", default="small,sdp,interval,batched,serve",
                     help="comma-separated sections after the headline: small, sdp, interval, batched, serve")
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-sample", type=int, default=40,
+                    help="the plain loop's service times are measured on every n-th request of the trace")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     args = ap.parse_args()
     if args.impl == "reference":

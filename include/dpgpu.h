@@ -323,8 +323,18 @@ dp_status serve_submit(void *srv, const dp_request *req, uint64_t *ticket);
 /* DP_EPENDING until the request finished; then fills *out.  Result pointers
  * stay valid until serve_release(ticket). */
 dp_status serve_poll(void *srv, uint64_t ticket, dp_result *out);
-/* Frees a finished request's device tables (returns its HBM to admission). */
+/* Frees a finished request's device tables (returns its HBM to admission).
+ * The free is ordered on the server's own stream only: work the caller has
+ * enqueued that still reads the tables (a copy on another stream) must have
+ * completed before this call -- synchronise first, or use
+ * serve_release_stream. */
 dp_status serve_release(void *srv, uint64_t ticket);
+/* serve_release for a caller that still has reads of the tables enqueued on
+ * `stream` (cudaStream_t as void*, NULL = legacy default stream): an event is
+ * recorded on that stream, and the tables' memory is freed only after it (and
+ * after the events of every other release of requests that share the same
+ * allocation).  Returns at once; DP_ECUDA if the event cannot be recorded. */
+dp_status serve_release_stream(void *srv, uint64_t ticket, void *stream);
 /* Current server time in seconds (the clock used by dp_result). */
 double serve_now(void *srv);
 /* Stops the scheduler after the queued work drains and frees everything. */

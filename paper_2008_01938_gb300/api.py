@@ -372,8 +372,12 @@ class Server:
         check(code)
         return res
 
-    def release(self, ticket):
-        check(native.load().serve_release(self._h, ticket))
+    def release(self, ticket, stream=None):
+        """Returns a finished request's tables to the server.  Reads of the
+        views from tables() that are still enqueued on ``stream`` (default:
+        torch's current stream) finish before the memory can be reused;
+        reads on another stream must be synchronised first."""
+        check(native.load().serve_release_stream(self._h, ticket, _stream_ptr(stream)))
 
     @staticmethod
     def tables(res, cost="i64"):

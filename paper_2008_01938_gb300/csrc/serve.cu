@@ -41,7 +41,21 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 struct DeviceBlock {  // one output allocation shared by the requests of a launch
   void* ptr = nullptr;
   int refs = 0;
+  std::vector<cudaEvent_t> readers;  // recorded on the streams of releases that named one
 };
+
+// Frees a block when its last request is released: on the server's first
+// stream, after every event recorded by a release on the caller's stream, so
+// that reads of the tables the caller enqueued before releasing complete
+// before the memory can be handed to another launch.
+void free_block(cudaStream_t st, DeviceBlock* b) {
+  for (cudaEvent_t ev : b->readers) {
+    cudaStreamWaitEvent(st, ev, 0);
+    cudaEventDestroy(ev);
+  }
+  b->readers.clear();
+  cudaFreeAsync(b->ptr, st);
+}
 
 struct Req {
   uint64_t ticket = 0;
@@ -200,23 +214,45 @@ dp_status launch_mcm_group(Server* S, const std::vector<Req*>& reqs, bool i64, L
   return DP_OK;
 }
 
+// A group of S-DP requests with one operator.  Requests long enough for the
+// chunked paths of sdp_solve (sdp_jump.cu for +, sdp_minjump.cu for min; the
+// same cost models decide) run through those, spread over the SMs; the
+// others share one launch of the S-DP kernel, one block each.  Everything is
+// enqueued on the launch's stream, so one event covers the group.
 dp_status launch_sdp_group(Server* S, const std::vector<Req*>& reqs, int op, Launch* L) {
   int threads = 32, kmax = 1, ring_log2 = 1;
-  bool ring_ok = true, kfull = !reqs.empty();
+  DevState* ds = nullptr;
+  dp_status rc0 = current_dev(&ds);
+  if (rc0 != DP_OK) return rc0;
+  std::vector<int> chunks(reqs.size(), 0);
+  std::vector<size_t> bat;  // requests of the shared launch
+  for (size_t b = 0; b < reqs.size(); ++b) {
+    const Req* r = reqs[b];
+    const int k = (int)r->offs.size();
+    if (r->n > r->offs[0])
+      chunks[b] = op == DP_OP_MIN ? sdp_min_jump_chunks(r->n, r->offs.data(), k, ds->sms)
+                                  : sdp_jump_chunks(r->n, r->offs.data(), k, ds->sms);
+    if (chunks[b] < 2) bat.push_back(b);
+  }
+  bool ring_ok = true, kfull = !bat.empty();
   std::vector<int64_t> st_off(reqs.size());
   int64_t cells = 0, noffs = 0;
   for (size_t b = 0; b < reqs.size(); ++b) {
     const Req* r = reqs[b];
     st_off[b] = cells;
     cells = (int64_t)align_up((size_t)(cells + std::max<int64_t>(r->n, r->offs[0])), 64);
+    noffs += (int64_t)r->offs.size();
+  }
+  for (size_t b : bat) {
+    const Req* r = reqs[b];
     kmax = std::max(kmax, (int)r->offs.size());
     kfull = kfull && (int)r->offs.size() == dpk::kSdpMaxKRegs;
     int th, lg;
     sdp_shape(r->offs[0], r->offs.back(), &th, &lg);
     threads = std::max(threads, th);
-    noffs += (int64_t)r->offs.size();
   }
-  for (const Req* r : reqs) {
+  for (size_t b : bat) {
+    const Req* r = reqs[b];
     const int W = std::min<int>(r->offs.back(), threads);
     int lg = 0;
     while ((1ll << lg) < (long long)r->offs[0] + W) ++lg;
@@ -225,8 +261,8 @@ dp_status launch_sdp_group(Server* S, const std::vector<Req*>& reqs, int op, Lau
   }
   size_t off = 0;
   auto take = [&](size_t b) { size_t o = off; off = align_up(off + std::max<size_t>(b, 16), 256); return o; };
-  const size_t o_offs = take((size_t)noffs * 4), o_insts = take(reqs.size() * sizeof(dpk::SdpInstDev));
-  const size_t o_stoff = take(reqs.size() * 8);
+  const size_t o_offs = take((size_t)noffs * 4), o_insts = take(std::max<size_t>(bat.size(), 1) * sizeof(dpk::SdpInstDev));
+  const size_t o_stoff = take(std::max<size_t>(bat.size(), 1) * 8);
   std::vector<size_t> o_pre(reqs.size());
   for (size_t b = 0; b < reqs.size(); ++b) o_pre[b] = take(reqs[b]->offs[0] * 4);
   const size_t in_bytes = off;
@@ -246,20 +282,27 @@ dp_status launch_sdp_group(Server* S, const std::vector<Req*>& reqs, int op, Lau
   uint8_t* ws = nullptr;
   if ((e = cudaMallocAsync(reinterpret_cast<void**>(&ws), in_bytes + 256, st)) != cudaSuccess)
     return fail_cuda(e, "serve: workspace allocation");
-  std::vector<dpk::SdpInstDev> insts(reqs.size());
+  std::vector<dpk::SdpInstDev> insts(bat.size());
+  std::vector<int64_t> bat_off(bat.size());
+  std::vector<int64_t> a_at(reqs.size());
   int64_t ao = 0;
   for (size_t b = 0; b < reqs.size(); ++b) {
     memcpy(hp + o_offs + ao * 4, reqs[b]->offs.data(), reqs[b]->offs.size() * 4);
-    insts[b].st = nullptr;
-    insts[b].n = reqs[b]->n;
-    insts[b].k = (int32_t)reqs[b]->offs.size();
-    insts[b].a = reinterpret_cast<const int32_t*>(ws + o_offs) + ao;
-    insts[b].a_off = (int32_t)ao;
+    a_at[b] = ao;
     ao += (int64_t)reqs[b]->offs.size();
     memcpy(hp + o_pre[b], reqs[b]->preset.data(), reqs[b]->offs[0] * 4);
   }
+  for (size_t i = 0; i < bat.size(); ++i) {
+    const size_t b = bat[i];
+    insts[i].st = nullptr;
+    insts[i].n = reqs[b]->n;
+    insts[i].k = (int32_t)reqs[b]->offs.size();
+    insts[i].a = reinterpret_cast<const int32_t*>(ws + o_offs) + a_at[b];
+    insts[i].a_off = (int32_t)a_at[b];
+    bat_off[i] = st_off[b];
+  }
   memcpy(hp + o_insts, insts.data(), insts.size() * sizeof(dpk::SdpInstDev));
-  memcpy(hp + o_stoff, st_off.data(), reqs.size() * 8);
+  memcpy(hp + o_stoff, bat_off.data(), bat_off.size() * 8);
   if ((e = cudaMemcpyAsync(ws, hp, in_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return fail_cuda(e, "serve: upload");
   int32_t* d_status = reinterpret_cast<int32_t*>(ws + in_bytes);
@@ -271,18 +314,30 @@ dp_status launch_sdp_group(Server* S, const std::vector<Req*>& reqs, int op, Lau
                        cudaSuccess)
       return fail_cuda(e, "serve: preset copy");
   }
-  dpk::SdpLaunchArgs args{};
-  args.insts = reinterpret_cast<const dpk::SdpInstDev*>(ws + o_insts);
-  args.one.k = kmax;
-  args.kfull = kfull;
-  args.ninst = (int32_t)reqs.size();
-  args.op = op;
-  args.threads = threads;
-  args.ring_log2 = ring_ok ? ring_log2 : 0;
-  args.st_all = st_all;
-  args.st_off = reinterpret_cast<const int64_t*>(ws + o_stoff);
-  args.status = d_status;
-  if ((e = dpk::launch_sdp(args, st)) != cudaSuccess) return fail_cuda(e, "serve: S-DP launch");
+  if (!bat.empty()) {
+    dpk::SdpLaunchArgs args{};
+    args.insts = reinterpret_cast<const dpk::SdpInstDev*>(ws + o_insts);
+    args.one.k = kmax;
+    args.kfull = kfull;
+    args.ninst = (int32_t)bat.size();
+    args.op = op;
+    args.threads = threads;
+    args.ring_log2 = ring_ok ? ring_log2 : 0;
+    args.st_all = st_all;
+    args.st_off = reinterpret_cast<const int64_t*>(ws + o_stoff);
+    args.status = d_status;
+    if ((e = dpk::launch_sdp(args, st)) != cudaSuccess) return fail_cuda(e, "serve: S-DP launch");
+  }
+  for (size_t b = 0; b < reqs.size(); ++b) {
+    if (chunks[b] < 2) continue;
+    const Req* r = reqs[b];
+    const dp_status rc = op == DP_OP_MIN
+                             ? sdp_min_jump(st_all + st_off[b], r->n, r->offs.data(), (int32_t)r->offs.size(), chunks[b],
+                                            d_status, st)
+                             : sdp_add_jump(st_all + st_off[b], r->n, r->offs.data(), (int32_t)r->offs.size(), chunks[b],
+                                            d_status, st);
+    if (rc != DP_OK) return rc;
+  }
   if ((e = cudaMemcpyAsync(L->status_host, d_status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return fail_cuda(e, "serve: status readback");
   cudaFreeAsync(ws, st);
@@ -481,20 +536,41 @@ dp_status serve_poll(void* srv, uint64_t ticket, dp_result* out) {
   return DP_OK;
 }
 
-dp_status serve_release(void* srv, uint64_t ticket) {
-  auto* S = static_cast<Server*>(srv);
-  if (!S) return fail(DP_EINVAL, "serve_release: NULL server");
+namespace {
+dp_status release_impl(Server* S, uint64_t ticket, bool after_stream, cudaStream_t reader) {
   std::lock_guard<std::mutex> lk(S->mu);
   auto it = S->all.find(ticket);
   if (it == S->all.end()) return fail(DP_EINVAL, "serve_release: unknown ticket %llu", (unsigned long long)ticket);
   Req* r = it->second;
   if (r->state != Req::DONE) return fail(DP_EPENDING, "serve_release: request still running");
-  if (r->block && --r->block->refs == 0) cudaFreeAsync(r->block->ptr, S->streams[0]);
+  if (r->block) {
+    if (after_stream) {
+      cudaEvent_t ev = nullptr;
+      cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess && (e = cudaEventRecord(ev, reader)) != cudaSuccess) cudaEventDestroy(ev);
+      if (e != cudaSuccess) return fail_cuda(e, "serve_release_stream: event on the caller's stream");
+      r->block->readers.push_back(ev);
+    }
+    if (--r->block->refs == 0) free_block(S->streams[0], r->block.get());
+  }
   S->resident -= r->footprint;
   S->inflight -= 1;
   S->all.erase(it);
   delete r;
   return DP_OK;
+}
+}  // namespace
+
+dp_status serve_release(void* srv, uint64_t ticket) {
+  auto* S = static_cast<Server*>(srv);
+  if (!S) return fail(DP_EINVAL, "serve_release: NULL server");
+  return release_impl(S, ticket, false, nullptr);
+}
+
+dp_status serve_release_stream(void* srv, uint64_t ticket, void* stream) {
+  auto* S = static_cast<Server*>(srv);
+  if (!S) return fail(DP_EINVAL, "serve_release_stream: NULL server");
+  return release_impl(S, ticket, true, static_cast<cudaStream_t>(stream));
 }
 
 double serve_now(void* srv) {
@@ -513,7 +589,7 @@ dp_status serve_destroy(void* srv) {
   S->th.join();
   for (auto& kv : S->all) {
     Req* r = kv.second;
-    if (r->block && --r->block->refs == 0) cudaFreeAsync(r->block->ptr, S->streams[0]);
+    if (r->block && --r->block->refs == 0) free_block(S->streams[0], r->block.get());
     delete r;
   }
   for (auto s : S->streams) {

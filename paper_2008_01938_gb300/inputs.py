@@ -54,12 +54,24 @@ def _mix(z: np.ndarray) -> np.ndarray:
         return z ^ (z >> np.uint64(31))
 
 
+def _mix_int(z: int) -> int:
+    """The same finaliser on one Python int (wrapping to 64 bits)."""
+    z = ((z ^ (z >> 30)) * _M1) & MASK64
+    z = ((z ^ (z >> 27)) * _M2) & MASK64
+    return z ^ (z >> 31)
+
+
 class SplitMix64:
-    """Counter-style splitmix64 stream: draw t is mix(seed + t * GAMMA)."""
+    """Counter-style splitmix64 stream: draw t is mix(seed + t * GAMMA).
+    Single draws take a scalar path with the same arithmetic (no arrays)."""
 
     def __init__(self, seed: int):
         self.seed = int(seed) & MASK64
         self.count = 0  # draws consumed so far
+
+    def _raw1(self) -> int:
+        self.count += 1
+        return _mix_int((self.seed + self.count * GAMMA) & MASK64)
 
     def raw(self, count: int) -> np.ndarray:
         """The next ``count`` 64-bit draws as a uint64 array."""
@@ -70,7 +82,23 @@ class SplitMix64:
         return _mix(z)
 
     def next_u64(self) -> int:
-        return int(self.raw(1)[0])
+        return self._raw1()
+
+    def randint1(self, lo: int, hi: int) -> int:
+        """One integer uniform in [lo, hi]: the draws randint(lo, hi, 1) uses."""
+        span = hi - lo + 1
+        assert 1 <= span <= (1 << 32)
+        if span == (1 << 32):
+            return (self._raw1() >> 32) + lo
+        thresh = ((1 << 32) - span) % span
+        while True:
+            prod = (self._raw1() >> 32) * span
+            if (prod & 0xFFFFFFFF) >= thresh:
+                return (prod >> 32) + lo
+
+    def uniform1(self) -> float:
+        """One double uniform in [0, 1): the draw uniform(1) uses."""
+        return (self._raw1() >> 11) * (1.0 / (1 << 53))
 
     def randint(self, lo: int, hi: int, count: int) -> np.ndarray:
         """``count`` integers uniform in [lo, hi] (inclusive), int64 array."""
@@ -106,7 +134,7 @@ class SplitMix64:
         return (self.raw(count) >> np.uint64(32)).astype(np.uint32)
 
     def log_uniform_int(self, lo: int, hi: int) -> int:
-        u = float(self.uniform(1)[0])
+        u = self.uniform1()
         a, b = math.log(lo), math.log(hi + 1)
         return min(hi, int(math.floor(math.exp(a + u * (b - a)))))
 
@@ -116,7 +144,7 @@ class SplitMix64:
         seen: list[int] = []
         have = set()
         while len(seen) < count:
-            v = int(self.randint(lo, hi, 1)[0])
+            v = self.randint1(lo, hi)
             if v not in have:
                 have.add(v)
                 seen.append(v)
@@ -232,11 +260,11 @@ def serve_trace(rate: float = 2000.0, duration: float = 60.0, seed: int = 4,
     out: list[Request] = []
     t = 0.0
     while True:
-        u = float(rng.uniform(1)[0])
+        u = rng.uniform1()
         t += -math.log(1.0 - u) / rate
         if t >= duration or (max_requests is not None and len(out) >= max_requests):
             break
-        kind = "mcm" if float(rng.uniform(1)[0]) < mcm_frac else "sdp"
+        kind = "mcm" if rng.uniform1() < mcm_frac else "sdp"
         if kind == "mcm":
             n = rng.log_uniform_int(*mcm_n)
             dims = rng.randint(mcm_d[0], mcm_d[1], n + 1).astype(np.int32)

@@ -28,7 +28,7 @@ HEADER_SYMBOLS = [
     "mcm_solve", "interval_dp_solve", "mcm_solve_noalloc", "mcm_traceback", "mcm_solve_host", "mcm_plan_create", "mcm_solve_batched",
     "mcm_plan_autotune", "mcm_plan_config", "mcm_plan_destroy",
     "sdp_solve", "sdp_solve_host", "sdp_plan_create", "sdp_solve_batched", "sdp_plan_destroy",
-    "serve_create", "serve_submit", "serve_poll", "serve_release", "serve_now", "serve_destroy",
+    "serve_create", "serve_submit", "serve_poll", "serve_release", "serve_release_stream", "serve_now", "serve_destroy",
 ]
 
 
@@ -108,6 +108,7 @@ def load(path: str | None = None):
             "serve_submit": ([vp, ctypes.POINTER(Request), ctypes.POINTER(u64)], ctypes.c_int),
             "serve_poll": ([vp, u64, ctypes.POINTER(Result)], ctypes.c_int),
             "serve_release": ([vp, u64], ctypes.c_int),
+            "serve_release_stream": ([vp, u64, vp], ctypes.c_int),
             "serve_now": ([vp], ctypes.c_double),
             "serve_destroy": ([vp], ctypes.c_int),
         }

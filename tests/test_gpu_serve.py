@@ -82,14 +82,18 @@ def test_mix_equals_alone(dp):
             assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1]), f"MCM n={r.n} differs"
         else:
             assert np.array_equal(got, want), f"S-DP n={r.n} differs"
-    # the small MCM requests also against the oracle
-    checked = 0
+    # the small MCM requests and every S-DP request also against the oracle
+    # (long S-DP requests take the chunked path in the server and alone)
+    checked = sdp_checked = 0
     for r, got in zip(trace, served):
         if r.kind == "mcm" and r.n <= 200:
             om, os_ = oracle.mcm(r.dims)
             assert np.array_equal(got[0].astype(np.int64), om) and np.array_equal(got[1], os_)
             checked += 1
-    assert checked >= 3
+        elif r.kind == "sdp":
+            assert np.array_equal(got, oracle.sdp(r.preset, r.n, r.offsets, "min")), f"S-DP n={r.n} vs oracle"
+            sdp_checked += 1
+    assert checked >= 3 and sdp_checked >= 3
 
 
 def test_admission_by_footprint(dp):
@@ -116,3 +120,51 @@ def test_admission_by_footprint(dp):
     assert int(m[0, -1].item()) == int(om[0, -1])
     srv.release(t2)
     srv.close()
+
+
+def test_release_after_async_reads(dp):
+    """Views of served tables are copied asynchronously on a side stream and
+    the requests released at once, under load (new requests keep arriving,
+    so freed memory is reused quickly): every copy still holds the request's
+    own result, because the release orders the free after the side stream's
+    pending work."""
+    import time
+    import torch
+    trace = inputs.serve_trace(rate=4000.0, duration=1.0, seed=13, mcm_n=(64, 400), sdp_n=(1 << 16, 1 << 17),
+                               max_requests=96)
+    srv = dp.Server(hbm_cap_bytes=8 << 30, max_inflight=1000, num_streams=4, max_batch=8)
+    side = torch.cuda.Stream()
+    pending = list(range(len(trace)))
+    live, copies = {}, {}
+    t_end = time.time() + 120
+    while pending or live:
+        assert time.time() < t_end, "server did not finish"
+        for _ in range(4):  # keep new work arriving while results are read
+            if pending:
+                i = pending.pop(0)
+                r = trace[i]
+                tk = srv.submit_mcm(r.dims) if r.kind == "mcm" else srv.submit_sdp(r.n, r.offsets, r.preset)
+                assert tk is not None
+                live[tk] = i
+        for tk in list(live):
+            res = srv.poll(tk)
+            if res is None:
+                continue
+            assert res.status == 0
+            i = live.pop(tk)
+            with torch.cuda.stream(side):
+                if trace[i].kind == "mcm":
+                    m, s = srv.tables(res)
+                    copies[i] = (m.clone(), s.clone())
+                else:
+                    copies[i] = srv.tables(res)[: trace[i].n].clone()
+            srv.release(tk, stream=side)
+        time.sleep(2e-4)
+    srv.close()
+    side.synchronize()
+    for i, r in enumerate(trace):
+        want = _alone(dp, r, "i64")
+        if r.kind == "mcm":
+            assert np.array_equal(copies[i][0].cpu().numpy(), want[0]) and np.array_equal(copies[i][1].cpu().numpy(), want[1])
+        else:
+            assert np.array_equal(copies[i].cpu().numpy().view(np.uint32), want)
