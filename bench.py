@@ -36,7 +36,6 @@ import hashlib
 import json
 import math
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -160,17 +159,16 @@ def _kernel_source_sha():
 
 
 def _profile_traffic():
-    """DRAM bytes per launch of the MCM kernel from the committed ncu summary,
-    valid only if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "mcm_main_n4096.md")
+    """DRAM bytes per launch of the MCM kernel from the machine-readable record
+    of the last ncu capture, valid only if it was taken on the current kernel
+    source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_records.json")
     if not os.path.exists(path):
         return None
-    txt = open(path).read()
-    msha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
-    mbytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not msha or not mbytes or msha.group(1) != _kernel_source_sha():
+    rec = json.load(open(path)).get("mcm_main_kernel<int32, unweighted>, n = 4096")
+    if not rec or rec.get("kernel_source_sha") != _kernel_source_sha():
         return None
-    return float(mbytes.group(1))
+    return float(rec["dram_bytes_per_launch"])
 
 
 def max_over_ranks(ms, device=None):
