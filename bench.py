@@ -375,7 +375,8 @@ def bench_sdp(dp, native, lib, dev, args):
         res[op] = {"cells_per_s": cells / (kms / 1e3), "kernel_ms": kms, "wall_ms": wall * 1e3,
                    "roofline": {"bound": "hbm", "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm,
                                 "unit": "GB/s", "frac": bytes_ / (kms / 1e3) / 1e9 / hbm,
-                                "note": "dependency chain of (n-a_1)/a_k steps bounds it, not HBM"}}
+                                "note": "the shared-memory reads of the recurrence steps bound it, not HBM "
+                                        "(smem_roofline)"}}
         av = np.ascontiguousarray(big.offsets.astype(np.int32))
         hook = lib.dp_test_sdp_jump_chunks if op == "add" else lib.dp_test_sdp_min_jump_chunks
         chunks = hook(big.n, ctypes.c_void_p(av.ctypes.data), int(av.size))
@@ -384,6 +385,13 @@ def bench_sdp(dp, native, lib, dev, args):
                        "Boolean products modulo the characteristic polynomial (bitsets) and range minima")
             res[op]["path"] = (f"chunks from jumped windows: {chunks} chunks side by side, their windows from "
                                f"{algebra} (time covers the whole path)")
+            nsm = min(chunks, args.probe["sms"])
+            peak_w = nsm * smem_peak
+            res[op]["smem_roofline"] = {"bound": f"shared memory of the {nsm} SMs the chunks run on",
+                                        "achieved": cells * k / (kms / 1e3) / 1e9, "peak": peak_w,
+                                        "unit": "G words/s", "frac": cells * k / (kms / 1e3) / 1e9 / peak_w,
+                                        "per_unit": f"{k} window reads per cell; the time also covers the "
+                                                    "windows' set-up launches"}
         else:
             res[op]["path"] = "step by step on one SM"
             res[op]["smem_roofline"] = {"bound": "shared memory of the one SM the chain runs on",
