@@ -187,6 +187,13 @@ __device__ __forceinline__ E sel4(int r, E a0, E a1, E a2, E a3) {
   }
 }
 
+// a[r] where p0 and p1 are bits 0 and 1 of r, already computed.
+template <typename E>
+__device__ __forceinline__ E sel4p(bool p0, bool p1, E a0, E a1, E a2, E a3) {
+  const E lo = p0 ? a1 : a0, hi = p0 ? a3 : a2;
+  return p1 ? hi : lo;
+}
+
 // Shared-memory store of v at 32-bit shared address addr when p holds.
 template <typename E>
 __device__ __forceinline__ void sts_if(bool p, uint32_t addr, E v) {
@@ -631,47 +638,56 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
             E pkc = (E)PKIp[SM::row(lane + T - 2)];
             bar_compute();
             if constexpr (!I64) {
-              // int32: the operands of step e + 1 (independent of the tile
-              // values) are loaded at the start of step e, so the barrier
-              // after the step does not wait for them, and each candidate is
-              // a multiply-add plus a fused add-and-minimum.
-#pragma unroll 1
-              for (int eb = -(T - 1); eb <= T - 2; eb += 4) {
+              // int32: the 62 steps are unrolled, so every shared-memory
+              // operand is a constant offset from a per-thread base. The
+              // operands of step e + 1 (independent of the tile values) are
+              // loaded at the start of step e, so the barrier after the step
+              // does not wait for them, and each candidate is a multiply-add
+              // plus a fused add-and-minimum. The row of the cell made final
+              // is chosen with predicates computed once: bit 0 of c0 - e
+              // flips every step, bit 1 repeats every four steps.
+              const E* Lb = Lp + SM::row(4 * w) * T + lane;                 // + u * T: L row u = 4w + e + r
+              const uint32_t* PJb = PKJp + SM::row(4 * w);                  // + u
+              const E* Ub = Up + SM::row(lane - 1) * SM::UPW + 4 * w;       // - (e + 1) * UPW: t = lane - 2 - e
+              const uint32_t* PIb = PKIp + SM::row(lane - 1);               // - (e + 1)
+              const E* Xcb = Xc + (T - 1) * T + lane;                       // + e * T: X[lane - e][lane]
+              const E* Xrb = Xr + (T - 1) * T + 4 * w;                      // + e * T: X[li][li + e]
+              const uint32_t sXcw = sXc + (uint32_t)((T * T + lane) * 4);      // + e * T * 4
+              const uint32_t sXrw = sXr + (uint32_t)((T * T + lane - 1) * 4);  // + e * (T - 1) * 4
+              const bool b0e = (c0 & 1) != 0;  // bit 0 of c0 - e for even e
+              bool b1[4];                      // bit 1 of c0 - e for e = k mod 4
 #pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4) {
-                  const int e = eb + s4;
-                  if (e <= T - 2) {
-                    if (e <= e_last) {
-                      const int dI = e + T - 1;
-                      const int un = 4 * w + e + 4;
-                      const E Rn = Lp[SM::row(un) * T + lane];
-                      const uint32_t Pn = PKJp[SM::row(un)];
-                      const int tn = lane - 2 - e;
-                      const Vec4<E> u4n = lds4(Up + SM::row(tn) * SM::UPW + 4 * w);
-                      const E pkcn = (E)PKIp[SM::row(tn)];
-                      const E xc = Xc[dI * T + lane];             // column operand X[lane - e][lane]
-                      const Vec4<E> x4 = lds4(Xr + dI * T + 4 * w);  // row operands X[li][li + e]
+              for (int k = 0; k < 4; ++k) b1[k] = ((c0 - k) & 2) != 0;
 #pragma unroll
-                      for (int r = 0; r < 4; ++r) {
-                        const int q = (1 + s4 + r) & 3;
-                        m[r] = __viaddmin_u32(u4.v[r] + wv[r] * pkc, xc, m[r]);
-                        m[r] = __viaddmin_u32(R[q] + wv[r] * (E)P[q], x4.v[r], m[r]);
-                      }
-                      // the lane's cell on diagonal e + 1 is final now
-                      const int rr = c0 - e;
-                      const bool own = (unsigned)rr <= 3u;
-                      E v = sel4(rr, m[0], m[1], m[2], m[3]);
-                      if constexpr (W) v += sel4(rr, wt[0], wt[1], wt[2], wt[3]);
-                      sts_if(own, sXr + (uint32_t)(((dI + 1) * T + 4 * w + rr) * (int)sizeof(E)), v);
-                      sts_if(own, sXc + (uint32_t)(((dI + 1) * T + lane) * (int)sizeof(E)), v);
-                      R[(1 + s4) & 3] = Rn;
-                      P[(1 + s4) & 3] = Pn;
-                      u4 = u4n;
-                      pkc = pkcn;
-                    }
-                    bar_compute();
+              for (int e = -(T - 1); e <= T - 2; ++e) {
+                const int s4 = (e + T - 1) & 3;
+                if (e <= e_last) {
+                  const E Rn = Lb[(e + 4) * T];
+                  const uint32_t Pn = PJb[e + 4];
+                  const Vec4<E> u4n = lds4(Ub - (e + 1) * SM::UPW);
+                  const E pkcn = (E)PIb[-(e + 1)];
+                  const E xc = Xcb[e * T];             // column operand X[lane - e][lane]
+                  const Vec4<E> x4 = lds4(Xrb + e * T);  // row operands X[li][li + e]
+#pragma unroll
+                  for (int r = 0; r < 4; ++r) {
+                    const int q = (1 + s4 + r) & 3;
+                    m[r] = __viaddmin_u32(u4.v[r] + wv[r] * pkc, xc, m[r]);
+                    m[r] = __viaddmin_u32(R[q] + wv[r] * (E)P[q], x4.v[r], m[r]);
                   }
+                  // the lane's cell on diagonal e + 1 (row 4w + c0 - e) is final now
+                  const bool p0 = (e & 1) ? !b0e : b0e;
+                  const bool p1 = b1[(e + 32) & 3];
+                  E v = sel4p(p0, p1, m[0], m[1], m[2], m[3]);
+                  if constexpr (W) v += sel4p(p0, p1, wt[0], wt[1], wt[2], wt[3]);
+                  const bool own = (unsigned)(c0 - e) <= 3u;
+                  sts_if(own, sXrw + (uint32_t)(e * (T - 1) * 4), v);
+                  sts_if(own, sXcw + (uint32_t)(e * T * 4), v);
+                  R[(1 + s4) & 3] = Rn;
+                  P[(1 + s4) & 3] = Pn;
+                  u4 = u4n;
+                  pkc = pkcn;
                 }
+                bar_compute();
               }
             } else {
 #pragma unroll 1
