@@ -133,12 +133,14 @@ McmStatic::~McmStatic() {
 namespace {
 using dpk::kMinBulkLevels;
 
-// Queue order: by the tile-diagonal at which a task becomes ready; within a
-// diagonal, finishers (the critical path) before bulk tasks.
+// Queue order: by bucket, a tile-diagonal no earlier than the one at which the
+// task becomes ready (every task therefore waits only for tasks queued before
+// it); within a bucket, finishers (the critical path) before bulk tasks, and
+// bulk tasks by the tile-diagonal of the finisher that needs them.
 struct SortKey {
-  int32_t bucket, kind, inst, I, J;
+  int32_t bucket, kind, need, inst, I, J;
   bool operator<(const SortKey& o) const {
-    return std::tie(bucket, kind, inst, I, J) < std::tie(o.bucket, o.kind, o.inst, o.I, o.J);
+    return std::tie(bucket, kind, need, inst, I, J) < std::tie(o.bucket, o.kind, o.need, o.inst, o.I, o.J);
   }
 };
 }  // namespace
@@ -198,7 +200,12 @@ dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared
             part.r_lo = (int16_t)r0;
             part.r_hi = (int16_t)r1;
             part.kind = 1;
-            items.push_back({SortKey{r1 + 1, 1, (int32_t)b, I, J}, part});
+            // ready at bucket r1 + 1; int32 parts other than the last one are
+            // deferred to kDeferBuckets diagonals before their finisher (int64
+            // plans keep the readiness order)
+            const bool last = r1 == fin_lo - 1;
+            const int bucket = (i64 || last) ? r1 + 1 : std::max(r1 + 1, D - dpk::kDeferBuckets);
+            items.push_back({SortKey{bucket, 1, i64 ? 0 : D, (int32_t)b, I, J}, part});
             ++nparts;
           };
           if (i64) {
@@ -218,7 +225,7 @@ dp_status mcm_build_static(const std::vector<int32_t>& ns, bool i64, std::shared
           fin.r_hi = (int16_t)rmax;
           fin.nparts = (int16_t)nparts;
         }
-        items.push_back({SortKey{D, 0, (int32_t)b, I, J}, fin});
+        items.push_back({SortKey{D, 0, 0, (int32_t)b, I, J}, fin});
       }
     }
   }
@@ -598,6 +605,23 @@ dp_status mcm_solve_host(const int32_t* p_host, int32_t n, dp_cost ct, void* m_h
   cudaFreeAsync(buf, st);
   if (rc == DP_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = fail_cuda(e, "mcm_solve_host: sync");
   return rc;
+}
+
+// Test hook (host only): the MCM work queue of a plan over chains of ns[0..m)
+// matrices, in pop order, 6 words per task: chain, I, J, kind (0 finisher,
+// 1 bulk part), first and last external level. Returns the number of tasks
+// (at most cap are written), or -1.
+int32_t dp_test_mcm_queue(const int32_t* ns, int32_t m, int32_t i64, int32_t* out, int32_t cap) {
+  if (!ns || m < 1) return -1;
+  std::shared_ptr<McmStatic> sp;
+  if (mcm_build_static(std::vector<int32_t>(ns, ns + m), i64 != 0, &sp, false) != DP_OK) return -1;
+  const int64_t nt = (int64_t)sp->tasks.size();
+  for (int64_t x = 0; x < nt && x < cap && out; ++x) {
+    const dpk::McmTask& t = sp->tasks[(size_t)x];
+    int32_t* o = out + 6 * x;
+    o[0] = t.inst, o[1] = t.I, o[2] = t.J, o[3] = t.kind, o[4] = t.r_lo, o[5] = t.r_hi;
+  }
+  return nt > INT32_MAX ? -1 : (int32_t)nt;
 }
 
 // Test hooks for the (x) = + jump path: the number of chunks sdp_solve would

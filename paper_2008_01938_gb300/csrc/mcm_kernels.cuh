@@ -65,6 +65,12 @@ constexpr int kMinBulkLevels = 2;
 // kLastPartLevels levels, and kLevelsPerPart-level parts cover the levels
 // below it.
 constexpr int kLastPartLevels = 4;
+// Queue position of the other int32 parts: not before they become ready, and
+// not earlier than kDeferBuckets tile-diagonals before their finisher. Work
+// that is not needed soon then waits behind the tasks of the chain in the
+// middle diagonals (where blocks are scarce) and fills the blocks that the
+// last diagonals leave idle.
+constexpr int kDeferBuckets = 3;
 
 struct McmInstDev {
   const int32_t* p;   // dims p[0..n] (set by the prologue)

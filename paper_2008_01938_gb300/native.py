@@ -92,6 +92,7 @@ def load(path: str | None = None):
             "mcm_plan_destroy": ([vp], ctypes.c_int),
             "dp_mcm_plan_tasks": ([vp], i64),
             "dp_test_host_range_device_address": ([vp, ctypes.c_size_t, ctypes.c_int], vp),
+            "dp_test_mcm_queue": ([vp, i32, i32, vp, i32], i32),
             "dp_test_sdp_jump_chunks": ([i64, vp, i32], i32),
             "dp_test_sdp_jump_plan": ([i64, vp, i32, i32, vp], i32),
             "dp_test_sdp_jump": ([vp, i64, vp, i32, i32, vp, vp], ctypes.c_int),

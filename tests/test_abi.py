@@ -155,3 +155,51 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(native, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         native.load(str(tmp_path / "nope.so"))
+
+
+def test_mcm_queue_orders_every_dependency_first(lib):
+    """The MCM work queue (host only): every tile has one finisher; its bulk
+    parts and the finisher cover the external levels (D+1)/2 .. D-1 exactly
+    once; and every task comes after the finishers of all tiles it reads and
+    a finisher after its own parts. Blocks pop tasks in queue order and wait
+    only for what they read, so this order is what keeps the persistent
+    kernel free of deadlock at any number of resident blocks (Section IV-B's
+    diagonal order at tile granularity, with bulk parts deferred towards the
+    finisher that needs them)."""
+    import ctypes
+    T = 32
+    for ns, i64 in [([4096], 0), ([33, 70, 161, 300, 1000, 2], 0), ([33, 70, 161, 300, 1000, 2], 1), ([512, 9], 1)]:
+        arr = np.asarray(ns, dtype=np.int32)
+        nt_total = lib.dp_test_mcm_queue(ctypes.c_void_p(arr.ctypes.data), len(ns), i64, None, 0)
+        assert nt_total > 0
+        out = np.zeros(6 * nt_total, dtype=np.int32)
+        assert lib.dp_test_mcm_queue(ctypes.c_void_p(arr.ctypes.data), len(ns), i64,
+                                     ctypes.c_void_p(out.ctypes.data), nt_total) == nt_total
+        q = out.reshape(-1, 6).tolist()
+        fin_pos, parts = {}, {}
+        for x, (c, I, J, kind, lo, hi) in enumerate(q):
+            if kind == 0:
+                assert (c, I, J) not in fin_pos
+                fin_pos[(c, I, J)] = x
+            else:
+                parts.setdefault((c, I, J), []).append((x, lo, hi))
+        for c, n in enumerate(ns):
+            nt = (n + T - 1) // T
+            assert sum(1 for key in fin_pos if key[0] == c) == nt * (nt + 1) // 2
+        for x, (c, I, J, kind, lo, hi) in enumerate(q):
+            D = J - I
+            for r in range(lo, hi + 1):
+                for K in {I + r, J - r}:
+                    if I < K < J:
+                        for tile in [(c, I, K), (c, K, J), (c, K + 1, J)]:
+                            assert fin_pos[tile] < x, (ns, i64, q[x], tile)
+            if kind == 0:
+                if D >= 1:
+                    for tile in [(c, I, I), (c, J, J), (c, I + 1, J)]:
+                        assert fin_pos[tile] < x, (ns, i64, q[x], tile)
+                levels = list(range(lo, hi + 1)) if D >= 2 else []
+                for (y, plo, phi) in parts.get((c, I, J), []):
+                    assert y < x
+                    levels += list(range(plo, phi + 1))
+                want = list(range((D + 1) // 2, D)) if D >= 2 else []
+                assert sorted(levels) == want, (ns, i64, q[x], sorted(levels))
