@@ -802,6 +802,22 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
               if constexpr (W) v -= sel4(r, wt[0], wt[1], wt[2], wt[3]);
               const E wr = sel4(r, wv[0], wv[1], wv[2], wv[3]);
               int k = -1;
+              if constexpr (!I64) {
+                // int32: four splits per round with independent loads, the
+                // smallest matching one kept; a lane stops after the first
+                // round with a match
+                for (int t0 = li; t0 <= T - 2 && k < 0; t0 += 4) {
+                  E c4[4];
+#pragma unroll
+                  for (int d = 0; d < 4; ++d) {
+                    const int t = t0 + d <= T - 2 ? t0 + d : T - 2;
+                    c4[d] = Up[SM::row(t) * SM::UPW + li] + Xc[(lane - t - 1 + T - 1) * T + lane] + wr * (E)PKIp[SM::row(t)];
+                  }
+#pragma unroll
+                  for (int d = 3; d >= 0; --d)
+                    if (t0 + d <= T - 2 && c4[d] == v) k = IT + t0 + d;
+                }
+              } else {
               for (int t = li; t <= T - 2; ++t) {
                 if (Up[SM::row(t) * SM::UPW + li] + Xc[(lane - t - 1 + T - 1) * T + lane] + wr * (E)PKIp[SM::row(t)] ==
                     v) {
@@ -809,17 +825,32 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
                   break;
                 }
               }
+              }
               if (k < 0 && (finU[(T - 1) * T + li] >> shiftv) + brow + wr * pI32 == v) k = IT + T - 1;
               if (k < 0) {
                 const unsigned long long ek = bestS[li * T + lane];
                 if ((E)(ek >> KB) == v) k = (int)(ek & kmask);
               }
               if (k < 0) {
+                if constexpr (!I64) {
+                  for (int u0 = 0; u0 < lane && k < 0; u0 += 4) {
+                    E c4[4];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                      const int u = u0 + d <= T - 2 ? u0 + d : T - 2;
+                      c4[d] = Xr[(u - li + T - 1) * T + li] + Lp[SM::row(u) * T + lane] + wr * (E)PKJp[SM::row(u)];
+                    }
+#pragma unroll
+                    for (int d = 3; d >= 0; --d)
+                      if (u0 + d < lane && c4[d] == v) k = JT + u0 + d;
+                  }
+                } else {
                 for (int u = 0; u < lane; ++u) {
                   if (Xr[(u - li + T - 1) * T + li] + Lp[SM::row(u) * T + lane] + wr * (E)PKJp[SM::row(u)] == v) {
                     k = JT + u;
                     break;
                   }
+                }
                 }
               }
               inst.s[i * nn + j] = (int16_t)k;
