@@ -70,8 +70,9 @@ constexpr int kZW = kTB + kSB + 32;     // staged z words
 __host__ __device__ constexpr int zpad(int i) { return i + 4 * (i >> 4); }
 constexpr int kZS = zpad(kZW) + 4;      // padded staging words
 
-// Batch item b is (b_hi, b_lo) = (b / nlo, b % nlo); each operand moves by
-// its lo stride per b_lo and its hi stride per b_hi.
+// Batch item b is (v, b_hi, b_lo): v = b / nvi (0 when nvi <= 0), then
+// (b_hi, b_lo) = (r / nlo, r % nlo) for r = b - v nvi; each operand moves by
+// its lo stride per b_lo, its hi stride per b_hi and its v stride per v.
 struct ToepArgs {
   const uint32_t* u;
   int64_t ustride, ustride_hi;
@@ -88,6 +89,8 @@ struct ToepArgs {
   int64_t nlo;
   uint32_t* zero;    // zero[0 .. zero_len) is cleared by the grid, for a later launch
   int64_t zero_len;
+  int64_t nvi;       // items per variant (<= 0: one variant)
+  int64_t ustride_v, zstride_v, ostride_v;
 };
 
 template <bool CONV>
@@ -101,13 +104,15 @@ __global__ void __launch_bounds__(kTT) toeplitz_kernel(const ToepArgs a) {
     for (int64_t i = blk * kTT + tid; i < a.zero_len; i += nthreads) a.zero[i] = 0u;
   }
   const int64_t T0 = (int64_t)blockIdx.x * kTB;
-  const int64_t b_hi = blockIdx.z / a.nlo, b_lo = blockIdx.z % a.nlo;
+  const int64_t bv = a.nvi > 0 ? (int64_t)blockIdx.z / a.nvi : 0;
+  const int64_t br = (int64_t)blockIdx.z - bv * (a.nvi > 0 ? a.nvi : 0);
+  const int64_t b_hi = br / a.nlo, b_lo = br % a.nlo;
   if (T0 >= a.tout) return;
   const int64_t Tw = T0 + (int64_t)(tid >> 5) * (32 * kTo);  // the warp's first output
-  const int64_t zo = b_hi * a.zstride_hi + b_lo * a.zstride;
+  const int64_t zo = bv * a.zstride_v + b_hi * a.zstride_hi + b_lo * a.zstride;
   const uint32_t* zb = a.z + zo;
   const int64_t zlen = a.zlen < a.zlim - zo ? a.zlen : a.zlim - zo;
-  const uint32_t* ub = a.u + b_hi * a.ustride_hi + b_lo * a.ustride;
+  const uint32_t* ub = a.u + bv * a.ustride_v + b_hi * a.ustride_hi + b_lo * a.ustride;
   uint32_t acc[kTo];
 #pragma unroll
   for (int q = 0; q < kTo; ++q) acc[q] = 0u;
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(kTT) toeplitz_kernel(const ToepArgs a) {
   // every output of the block is written (zero where no piece contributed);
   // with the split range divided between blocks (gridDim.y > 1) the pieces'
   // sums are added into a zeroed buffer
-  const int64_t oo = b_hi * a.ostride_hi + b_lo * a.ostride;
+  const int64_t oo = bv * a.ostride_v + b_hi * a.ostride_hi + b_lo * a.ostride;
   uint32_t* ob = a.out + oo;
   const bool split = gridDim.y > 1;
 #pragma unroll
@@ -177,6 +182,50 @@ __global__ void __launch_bounds__(kTT) toeplitz_kernel(const ToepArgs a) {
         ob[t] = acc[q];
     }
   }
+}
+
+// Transposed Karatsuba for a batch of middle products out[t] = sum_{s < 2h}
+// u[s] z[t + s], t < 2h (rows (hi, lo): u by lo, z by hi): with u = u0 | u1
+// and z viewed from 0, h and 2h,
+//   out[t]     = P0[t] + P1[t],  out[h + t] = P0[t] + P2[t]   (t < h),
+//   P0 = M(u0 + u1, z[h..]),  P1 = M(u0, z[..] - z[h..]),  P2 = M(u1, z[2h..] - z[h..]),
+// three middle products of half the size (three quarters of the
+// multiply-adds); exact over Z/2^32. This kernel lays out the operands of
+// the three as variants v = 0, 1, 2 of one batch: ku[v][lo][s] (s < h) and
+// kz[v][hi][i] (i < 2h - 1, rows of 2h words), with z read as 0 outside
+// [0, zlen) and where (its offset from z) + i >= zlim.
+__global__ void __launch_bounds__(256) kara_prep_kernel(const uint32_t* u, int64_t us, int64_t nlo, const uint32_t* z,
+                                                        int64_t zs_hi, int64_t zlen, int64_t zlim, int64_t nhi,
+                                                        int64_t h, uint32_t* ku, uint32_t* kz) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t b = blockIdx.y;
+  if (b < nlo && x < h) {
+    const uint32_t u0 = u[b * us + x], u1 = u[b * us + h + x];
+    ku[b * h + x] = u0 + u1;
+    ku[(nlo + b) * h + x] = u0;
+    ku[(2 * nlo + b) * h + x] = u1;
+  }
+  if (b < nhi && x < 2 * h - 1) {
+    const int64_t zo = b * zs_hi;
+    auto Z = [&](int64_t i) { return (i < zlen && zo + i < zlim) ? z[zo + i] : 0u; };
+    const uint32_t mid = Z(h + x);
+    kz[b * 2 * h + x] = mid;
+    kz[(nhi + b) * 2 * h + x] = Z(x) - mid;
+    kz[(2 * nhi + b) * 2 * h + x] = Z(2 * h + x) - mid;
+  }
+}
+
+// out[r][t] = P0[r][t] + P1[r][t], out[r][h + t] = P0[r][t] + P2[r][t] for
+// t < h, rows r of 2h words; the products in kout[v][r][t] (the last step of
+// the transposed Karatsuba above).
+__global__ void __launch_bounds__(256) kara_combine_kernel(uint32_t* out, const uint32_t* kout, int64_t rows,
+                                                           int64_t h) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r = blockIdx.y;
+  if (t >= h) return;
+  const uint32_t p0 = kout[r * h + t];
+  out[r * 2 * h + t] = p0 + kout[(rows + r) * h + t];
+  out[r * 2 * h + h + t] = p0 + kout[(2 * rows + r) * h + t];
 }
 
 // r[b][e] = c[b][e] + sum_j h[b][e + a_j - A] over the j with A <= e + a_j <=
@@ -477,6 +526,14 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   const size_t o_hf = take((size_t)nb * HS * 4);
   const int64_t nwin = std::max<int64_t>((int64_t)P1e * P2, 2);     // window scratch rows
   const size_t o_win = take((size_t)nwin * A * 4);
+  // the windows' middle products by one transposed Karatsuba step (A even,
+  // and each half still a full output block of the Toeplitz kernel)
+  const int64_t kh = A / 2;
+  const bool kara = A % 2 == 0 && kh >= dpk::kTB;
+  const int64_t knlo = std::max<int64_t>({(int64_t)P1e, (int64_t)P2, 1});
+  const size_t o_ku = take(kara ? (size_t)3 * knlo * kh * 4 : 0);
+  const size_t o_kz = take(kara ? (size_t)3 * P1e * 2 * kh * 4 : 0);
+  const size_t o_kout = take(kara ? (size_t)3 * nwin * kh * 4 : 0);
   const size_t o_insts = take((size_t)P * sizeof(dpk::SdpInstDev));
   const size_t o_ext = take((size_t)std::max(P1e - 1, 1) * sizeof(dpk::SdpInstDev));
   const size_t o_pre = take(2 * sizeof(dpk::SdpInstDev));
@@ -490,6 +547,9 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   uint32_t* prod = reinterpret_cast<uint32_t*>(ws + o_prod);
   uint32_t* hf = reinterpret_cast<uint32_t*>(ws + o_hf);
   uint32_t* win = reinterpret_cast<uint32_t*>(ws + o_win);
+  uint32_t* ku = reinterpret_cast<uint32_t*>(ws + o_ku);
+  uint32_t* kz = reinterpret_cast<uint32_t*>(ws + o_kz);
+  uint32_t* kout = reinterpret_cast<uint32_t*>(ws + o_kout);
   auto* insts = reinterpret_cast<dpk::SdpInstDev*>(ws + o_insts);
   auto* ext_insts = reinterpret_cast<dpk::SdpInstDev*>(ws + o_ext);
   auto* pre_insts = reinterpret_cast<dpk::SdpInstDev*>(ws + o_pre);
@@ -584,6 +644,42 @@ dp_status sdp_add_jump(uint32_t* ST, int64_t n, const int32_t* a, int32_t k, int
   // row (hi, lo), t < A = sum_s U_(hi, lo)[s] ST[hi zs_hi + s + t]
   auto windows = [&](const uint32_t* U, int64_t us, int64_t us_hi, int64_t zs_hi, int64_t nhi, int64_t nlo) {
     if (nhi * nlo <= 0) return cudaSuccess;
+    if (kara && us_hi == 0) {
+      // the three half-size products as one launch of 3 rows items; the
+      // split count divides the pieces evenly
+      const int64_t rows = nhi * nlo;
+      const int64_t pieces = (kh + dpk::kSB - 1) / dpk::kSB;
+      const int64_t want = std::max<int64_t>(1, (5 * (int64_t)ds->sms) / (3 * rows));
+      int64_t sp = 1;
+      for (int64_t d = 1; d <= pieces && d <= want; ++d)
+        if (pieces % d == 0) sp = d;
+      if (sp > 1 && (e = cudaMemsetAsync(kout, 0, (size_t)3 * rows * kh * 4, st)) != cudaSuccess) return e;
+      dpk::kara_prep_kernel<<<dim3((unsigned)((2 * kh + 255) / 256), (unsigned)std::max(nlo, nhi)), 256, 0, st>>>(
+          U, us, nlo, ST, zs_hi, 2 * (int64_t)A - 1, n, nhi, kh, ku, kz);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      ToepArgs tk{};
+      tk.u = ku;
+      tk.ustride = kh;
+      tk.ustride_v = nlo * kh;
+      tk.S = kh;
+      tk.z = kz;
+      tk.zstride_hi = 2 * kh;
+      tk.zstride_v = nhi * 2 * kh;
+      tk.zlen = 2 * kh - 1;
+      tk.zlim = INT64_MAX;
+      tk.out = kout;
+      tk.ostride = kh;
+      tk.ostride_hi = nlo * kh;
+      tk.ostride_v = rows * kh;
+      tk.tout = kh;
+      tk.olim = INT64_MAX;
+      tk.nlo = nlo;
+      tk.nvi = rows;
+      if ((e = dpk::toeplitz(false, tk, 3 * rows, (int)sp, st)) != cudaSuccess) return e;
+      dpk::kara_combine_kernel<<<dim3((unsigned)((kh + 255) / 256), (unsigned)rows), 256, 0, st>>>(win, kout, rows,
+                                                                                                   kh);
+      return cudaGetLastError();
+    }
     const int64_t tb = (A + dpk::kTB - 1) / dpk::kTB;
     const int sp = dpk::split_count(A, tb, nhi * nlo, ds->sms);
     if ((e = cudaMemsetAsync(win, 0, (size_t)nhi * nlo * A * 4, st)) != cudaSuccess) return e;

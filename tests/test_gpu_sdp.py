@@ -88,6 +88,8 @@ JUMP_CASES = [
     (962, [40, 33, 17, 2], 12),             # last chunk (38 cells) shorter than the window
     (165, [9, 4, 3], 5),                    # last chunk of 5 cells
     (400000, (16, 64, 4096, 9), 40),
+    (1000000, (32, 1024, 8192, 3), 40),     # a_1 = 8192: windows by the transposed Karatsuba step
+    (400000, (32, 1024, 8192, 4), 20),      # the same, chunks of the least length (2 a_1)
 ]
 
 

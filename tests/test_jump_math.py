@@ -112,3 +112,33 @@ def test_chi_reduces_the_recurrence():
         ch = chi(a)
         for m in range(0, 5 * A):
             assert sum(ch[i] * st[m + i] for i in range(A + 1)) % MOD == 0
+
+
+def middle_product(u, z):
+    """out[t] = sum_s u[s] z[t + s] for t < len(u) (z has 2 len(u) - 1 values)."""
+    A = len(u)
+    return [sum(u[s] * z[t + s] for s in range(A)) % MOD for t in range(A)]
+
+
+def test_transposed_karatsuba_middle_product():
+    """(K) The windows and reductions of the (+) path are middle products
+    out[t] = sum_s u[s] z[t + s]. With u = u0 | u1 and z viewed from 0, h
+    and 2h (h = len(u) / 2), three half-size middle products give them:
+    P1 = M(u0 + u1, z[h:]), P2 = M(u0, z[:] - z[h:]), P3 = M(u1, z[2h:] -
+    z[h:]); out[:h] = P1 + P2 and out[h:] = P1 + P3. Exact over Z/2^32,
+    including values near 2^32 (checked against the direct sum)."""
+    rng = random.Random(11)
+    for A in [2, 4, 8, 16, 64]:
+        for _ in range(5):
+            u = [rng.randrange(MOD) for _ in range(A)]
+            z = [rng.randrange(MOD) for _ in range(2 * A - 1)]
+            h = A // 2
+            zz = z + [0]  # one slack value so the views below have 2h - 1 entries each
+            u0, u1 = u[:h], u[h:]
+            up = [(x + y) % MOD for x, y in zip(u0, u1)]
+            z1 = zz[h:h + 2 * h - 1]
+            d0 = [(zz[i] - zz[h + i]) % MOD for i in range(2 * h - 1)]
+            d2 = [(zz[2 * h + i] - zz[h + i]) % MOD for i in range(2 * h - 1)]
+            p1, p2, p3 = middle_product(up, z1), middle_product(u0, d0), middle_product(u1, d2)
+            got = [(x + y) % MOD for x, y in zip(p1, p2)] + [(x + y) % MOD for x, y in zip(p1, p3)]
+            assert got == middle_product(u, z), A
