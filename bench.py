@@ -123,13 +123,14 @@ def measure_int32_peak(lib, native, stream):
     kind counted in SM cycles.  The peak is the combined rate of both integer
     pipes (two-input adds, which the compiler spreads over the ALU and FMA
     pipes) at the maximum SM clock."""
-    out = (ctypes.c_double * 9)()
-    native.check(lib.dp_measure_int32_rates(out, 9, ctypes.c_void_p(stream.cuda_stream)))
+    out = (ctypes.c_double * 10)()
+    native.check(lib.dp_measure_int32_rates(out, 10, ctypes.c_void_p(stream.cuda_stream)))
     rec = {"sms": int(out[6]),
            "lanes_per_clk_sm": {"add3_alu_pipe": round(out[0], 2), "imad_fma_pipe": round(out[1], 2),
                                 "min3_alu_pipe": round(out[2], 2), "add2_both_pipes": round(out[3], 2),
                                 "add3_imad_interleaved": round(out[4], 2)},
            "bulk_loop_split_evals_per_clk_sm": round(out[5], 3),
+           "bulk_loop_i64_split_evals_per_clk_sm": round(out[9], 3),
            "probe_clock_mhz": round(out[7], 1), "max_sm_clock_mhz": out[8]}
     rec["peak_tops"] = rec["sms"] * out[3] * out[8] * 1e6 / 1e12
     rec["bulk_loop_ceiling_tops"] = INT_OPS_PER_EVAL * rec["sms"] * out[5] * out[8] * 1e6 / 1e12
@@ -559,7 +560,21 @@ def bench_batched(dp, native, lib, dev, args):
     t_plain = e0.elapsed_time(e1) / 1e3
     dp.sync_status()
     plan.destroy()
+    # roofline: the int64 solver's own bulk loop, measured by the probe (split
+    # evaluations per clock per SM at two resident blocks) on every SM at the
+    # maximum clock; an int64 split evaluation is several INT32 instructions
+    roof = None
+    probe = getattr(args, "probe", None)
+    if probe and probe.get("bulk_loop_i64_split_evals_per_clk_sm"):
+        rate = probe["bulk_loop_i64_split_evals_per_clk_sm"]
+        peak = probe["sms"] * rate * probe["max_sm_clock_mhz"] * 1e6
+        roof = {"bound": "alu", "achieved": total / t_graph, "peak": peak, "unit": "split-evals/s (int64)",
+                "frac": round(total / t_graph / peak, 4), "kernel": "mcm_main_kernel<int64> (graph replay)",
+                "peak_basis": (f"measured: {probe['sms']} SMs x {rate:.2f} int64 split evaluations/clk/SM "
+                               f"(the int64 solver's bulk loop on a staged panel, 2 blocks/SM) x "
+                               f"{probe['max_sm_clock_mhz']:.0f} MHz")}
     return {"workload": "10,000 chains, n log-uniform [8,512], dims U[1,1000] seed 3, int64 costs",
+            "roofline": roof,
             "split_evals": total, "graph_evals_per_s": total / t_graph, "graph_ms": t_graph * 1e3,
             "no_graph_ms": t_nograph * 1e3,
             "plain_loop_evals_per_s": total / t_plain, "plain_loop_ms": t_plain * 1e3,

@@ -85,7 +85,8 @@ dp_status dp_profile_end(double *mcm_ms, int64_t *mcm_launches, double *sdp_ms, 
  * measurement utility).  Every SM is kept full of independent dependency
  * chains of one instruction kind; SM clock cycles are counted around the loop
  * on the device, so the lane figures do not depend on the clock.  Fills
- * out[0..8] (host doubles, nout >= 9, else DP_EINVAL):
+ * out[0..8] (host doubles, nout >= 9, else DP_EINVAL), and out[9] when
+ * nout >= 10:
  *   out[0]  three-input integer add (ALU pipe), lanes per clock per SM
  *   out[1]  integer multiply-add (FMA pipe), lanes per clock per SM
  *   out[2]  three-way unsigned minimum (ALU pipe), lanes per clock per SM
@@ -100,8 +101,12 @@ dp_status dp_profile_end(double *mcm_ms, int64_t *mcm_launches, double *sdp_ms, 
  *   out[6]  SM count of the device (cudaDevAttrMultiProcessorCount)
  *   out[7]  SM clock seen during the probes, MHz (cycles / event time)
  *   out[8]  the device's reported maximum SM clock, MHz
- * Runs twelve short launches on `stream` (about 30 ms in all) and waits for
- * them; a 16-byte stream-ordered allocation holds the cycle counts. */
+ *   out[9]  the int64 solver's bulk loop (64-bit packed keys, two resident
+ *           blocks per SM as in the int64 solver), split evaluations per
+ *           clock per SM
+ * Runs twelve short launches (fourteen with out[9]) on `stream`, about 30 ms
+ * in all, and waits for them; a 16-byte stream-ordered allocation holds the
+ * cycle counts. */
 dp_status dp_measure_int32_rates(double *out, int32_t nout, void *stream);
 
 /* ------------------------------------------------------------------------- */

@@ -147,25 +147,85 @@ __global__ void __launch_bounds__(kProbeThreads, kBulkBlocksPerSm)
   if (x == 0x123456789ull) atomicAdd(&out->sink, 1ull);
 }
 
+// The int64 solver's bulk loop (seg_i64): 64-bit packed (value, k) entries
+// on a shared-memory panel, a 64-bit multiply-add of the weight and a 64-bit
+// minimum per split, 4 x 2 cells per thread, two resident blocks per SM as
+// in the int64 solver.
+constexpr int kBulk64BlocksPerSm = 2;
+__global__ void __launch_bounds__(kProbeThreads, kBulk64BlocksPerSm)
+    bulk64_rate_kernel(ProbeOut* out, uint32_t seed, int trips) {
+  constexpr int T = 32;
+  __shared__ __align__(16) unsigned long long A[T * T], B[T * T];
+  __shared__ uint32_t PK[T];
+  for (int x = threadIdx.x; x < T * T; x += blockDim.x) {
+    A[x] = ((unsigned long long)((seed * (x + 7u)) & 0x7FFFFFu) << 16) | (unsigned)(x & 1023);
+    B[x] = ((unsigned long long)((seed * (x + 3u)) & 0x3FFFFFu) << 16);
+  }
+  if (threadIdx.x < T) PK[threadIdx.x] = (threadIdx.x % 31u) + 1u;
+  const int tg = threadIdx.x & 127, ty = tg >> 4, tx = tg & 15;
+  uint32_t P[4][2];
+  unsigned long long best[4][2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      P[r][c] = (((seed >> (2 * r + c)) & 1023u) | 1u) << 16;
+      best[r][c] = ~0ull;
+    }
+  __syncthreads();
+  const long long t0 = clock64();
+#pragma unroll 1
+  for (int it = 0; it < trips; ++it) {
+#pragma unroll 4
+    for (int kk = 0; kk < T; ++kk) {
+      const ulonglong2 a01 = *reinterpret_cast<const ulonglong2*>(A + kk * T + 4 * ty);
+      const ulonglong2 a23 = *reinterpret_cast<const ulonglong2*>(A + kk * T + 4 * ty + 2);
+      const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(B + kk * T + 2 * tx);
+      const uint32_t pk = PK[kk];
+      const unsigned long long av[4] = {a01.x, a01.y, a23.x, a23.y};
+      const unsigned long long bv[2] = {b.x, b.y};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const unsigned long long cand = (unsigned long long)P[r][c] * pk + av[r] + bv[c];
+          best[r][c] = best[r][c] < cand ? best[r][c] : cand;
+        }
+    }
+    // a different panel word each trip, so nothing is loop-invariant
+    if (threadIdx.x == 0) PK[it & 31] += 1u;
+    __syncthreads();
+  }
+  const long long t1 = clock64();
+  unsigned long long x = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) x ^= best[r][c];
+  if (threadIdx.x == 0) atomicMax(&out->cycles_max, (unsigned long long)(t1 - t0));
+  if (x == 0x123456789ull) atomicAdd(&out->sink, 1ull);
+}
+
 }  // namespace
 
 using namespace dph;
 
 extern "C" dp_status dp_measure_int32_rates(double* out, int32_t nout, void* stream) {
   if (!out || nout < 9) return fail(DP_EINVAL, "dp_measure_int32_rates: out must hold 9 values");
+  const int nprobes = nout >= 10 ? 7 : 6;  // probe 6 (the int64 bulk loop) when out has room for it
   DevState* ds = nullptr;
   dp_status rc = current_dev(&ds);
   if (rc != DP_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  constexpr int kProbes = 6;
-  int occ[kProbes] = {0, 0, 0, 0, 0, 0};
+  int occ[7] = {0, 0, 0, 0, 0, 0, 0};
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], int32_rate_kernel<0>, kProbeThreads, 0)) != cudaSuccess ||
       (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], int32_rate_kernel<1>, kProbeThreads, 0)) != cudaSuccess ||
       (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], int32_rate_kernel<2>, kProbeThreads, 0)) != cudaSuccess ||
       (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], int32_rate_kernel<3>, kProbeThreads, 0)) != cudaSuccess ||
       (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[4], int32_rate_kernel<4>, kProbeThreads, 0)) != cudaSuccess ||
-      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[5], bulk_rate_kernel, kProbeThreads, 0)) != cudaSuccess)
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[5], bulk_rate_kernel, kProbeThreads, 0)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[6], bulk64_rate_kernel, kProbeThreads, 0)) != cudaSuccess)
     return fail_cuda(e, "dp_measure_int32_rates: occupancy");
   ProbeOut* d = nullptr;
   if ((e = cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(ProbeOut), st)) != cudaSuccess)
@@ -176,12 +236,12 @@ extern "C" dp_status dp_measure_int32_rates(double* out, int32_t nout, void* str
     return fail_cuda(e, "dp_measure_int32_rates: events");
   }
   double clk_sum = 0.0;
-  for (int op = 0; op < kProbes && rc == DP_OK; ++op) {
+  for (int op = 0; op < nprobes && rc == DP_OK; ++op) {
     // every block resident at once: one block per (SM, slot), no second wave
-    const int want = op == 5 ? kBulkBlocksPerSm : kProbeBlocksPerSm;
+    const int want = op == 5 ? kBulkBlocksPerSm : op == 6 ? kBulk64BlocksPerSm : kProbeBlocksPerSm;
     const int bps = occ[op] < want ? occ[op] : want;
     const int grid = ds->sms * (bps > 0 ? bps : 1);
-    const int trips = op == 5 ? 1024 : 2048;
+    const int trips = op >= 5 ? 1024 : 2048;
     for (int rep = 0; rep < 2 && rc == DP_OK; ++rep) {  // the first launch warms up
       cudaMemsetAsync(d, 0, sizeof(ProbeOut), st);
       cudaEventRecord(e0, st);
@@ -191,7 +251,8 @@ extern "C" dp_status dp_measure_int32_rates(double* out, int32_t nout, void* str
         case 2: int32_rate_kernel<2><<<grid, kProbeThreads, 0, st>>>(d, 0x2545F491u, trips); break;
         case 3: int32_rate_kernel<3><<<grid, kProbeThreads, 0, st>>>(d, 0x2545F491u, trips); break;
         case 4: int32_rate_kernel<4><<<grid, kProbeThreads, 0, st>>>(d, 0x2545F491u, trips); break;
-        default: bulk_rate_kernel<<<grid, kProbeThreads, 0, st>>>(d, 0x2545F491u, trips); break;
+        case 5: bulk_rate_kernel<<<grid, kProbeThreads, 0, st>>>(d, 0x2545F491u, trips); break;
+        default: bulk64_rate_kernel<<<grid, kProbeThreads, 0, st>>>(d, 0x2545F491u, trips); break;
       }
       cudaEventRecord(e1, st);
       if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
@@ -207,9 +268,9 @@ extern "C" dp_status dp_measure_int32_rates(double* out, int32_t nout, void* str
       }
       if (rep == 0 || h.cycles_max == 0) continue;
       const double threads_per_sm = (double)bps * kProbeThreads;
-      // instructions (probes 0-4) or split evaluations (probe 5) per thread
-      const double per_thread = op == 5 ? (double)trips * 32.0 * 8.0 : (double)trips * kUnroll * kChains;
-      out[op] = threads_per_sm * per_thread / (double)h.cycles_max;
+      // instructions (probes 0-4) or split evaluations (probes 5, 6) per thread
+      const double per_thread = op >= 5 ? (double)trips * 32.0 * 8.0 : (double)trips * kUnroll * kChains;
+      out[op == 6 ? 9 : op] = threads_per_sm * per_thread / (double)h.cycles_max;
       clk_sum += (double)h.cycles_max / (ms * 1e3);  // MHz (the slowest block spans about the launch)
     }
   }
@@ -218,7 +279,7 @@ extern "C" dp_status dp_measure_int32_rates(double* out, int32_t nout, void* str
   cudaFreeAsync(d, st);
   if (rc != DP_OK) return rc;
   out[6] = (double)ds->sms;
-  out[7] = clk_sum / kProbes;
+  out[7] = clk_sum / nprobes;
   int clk_khz = 0;
   cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, ds->device);
   out[8] = clk_khz / 1e3;

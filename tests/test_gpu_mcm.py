@@ -327,3 +327,26 @@ def test_batched_full_config(dp):
     assert _sha(m_all.astype("<i8")) == g["m_sha256_concat"]
     assert _sha(s_all.astype("<i2")) == g["s_sha256_concat"]
     plan.destroy()
+
+
+def test_int32_rate_probe(dp):
+    """The roofline's measured denominators: every rate positive and below
+    the issue limit of the SM (4 warp instructions per clock, 128 lanes), the
+    SM count that of the device, the int64 bulk loop only with room for it,
+    and DP_EINVAL for a buffer of fewer than 9 values."""
+    import ctypes
+    import torch
+    from paper_2008_01938_gb300 import native
+    lib = native.load()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = (ctypes.c_double * 10)(*([-1.0] * 10))
+    native.check(lib.dp_measure_int32_rates(out, 10, st))
+    assert int(out[6]) == torch.cuda.get_device_properties(0).multi_processor_count
+    for i in [0, 1, 2, 3, 4]:
+        assert 0 < out[i] <= 130, (i, out[i])
+    assert 0 < out[5] <= 64 and 0 < out[9] < out[5], (out[5], out[9])
+    assert out[7] > 0 and out[8] > 0
+    nine = (ctypes.c_double * 10)(*([-1.0] * 10))
+    native.check(lib.dp_measure_int32_rates(nine, 9, st))
+    assert nine[9] == -1.0 and nine[5] > 0
+    assert lib.dp_measure_int32_rates(nine, 8, st) == 1
