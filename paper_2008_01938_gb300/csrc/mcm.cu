@@ -794,13 +794,25 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
             const unsigned long long kmask = (1ull << KB) - 1ull;
 #pragma unroll 1
             for (int r = 0; r < 4; ++r) {
-              const int li = 4 * w + r;
+              // int32: warp w scans rows w, w + 8, w + 16 and w + 24, a mix of
+              // long and short column scans, so that the warps finish together
+              // (the value, weight and multiplier of the row are read again);
+              // int64: the warp's own rows 4w .. 4w + 3
+              const int li = I64 ? 4 * w + r : w + 8 * r;
               const int64_t i = IT + li, j = JT + lane;
               if (i >= nn || j >= nn) continue;
               // (register arrays are read through sel4: a runtime index would move them to local memory)
-              E v = sel4(r, vals[0], vals[1], vals[2], vals[3]);  // the minimum, less the cell's own weight
-              if constexpr (W) v -= sel4(r, wt[0], wt[1], wt[2], wt[3]);
-              const E wr = sel4(r, wv[0], wv[1], wv[2], wv[3]);
+              E v;   // the minimum, less the cell's own weight
+              E wr;  // the row's multiplier p[i] p[j+1]
+              if constexpr (I64) {
+                v = sel4(r, vals[0], vals[1], vals[2], vals[3]);
+                if constexpr (W) v -= sel4(r, wt[0], wt[1], wt[2], wt[3]);
+                wr = sel4(r, wv[0], wv[1], wv[2], wv[3]);
+              } else {
+                v = Xc[(lane - li + T - 1) * T + lane];
+                if constexpr (W) v -= static_cast<const E*>(inst.w)[i * inst.n + j];
+                wr = (E)finPP[li] * pj1;
+              }
               int k = -1;
               if constexpr (!I64) {
                 // int32: four splits per round with independent loads, the
