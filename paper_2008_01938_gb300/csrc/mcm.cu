@@ -870,8 +870,56 @@ __global__ void __launch_bounds__(kMcmThreads, I64 ? 2 : 3) mcm_main_kernel(cons
           } else {
             // diagonal tile: ordinary MCM on the 32-matrix sub-chain
             const E pj1d = (E)(finPKI[lane] >> shiftv);
+            bool keyed = false;
+            if constexpr (!I64) {
+              if (S == 5) {
+                // int32 with a 5-bit shift: a cell's running minimum is one
+                // 32-bit key (value << 5) + (k - IT), whose unsigned minimum
+                // keeps the smallest split on ties, as the 64-bit keys below
+                // do; final values are stored shifted in Xv, and a candidate
+                // whose operands are not both final is not taken (a select,
+                // no branch)
+                uint32_t* Xs = reinterpret_cast<uint32_t*>(Xv);
+                uint32_t key[4], pij[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                  key[r] = 0xFFFFFFFFu;
+                  pij[r] = pi[r] * pj1d;
+                }
 #pragma unroll 1
-            for (int e = 0; e <= T - 2; ++e) {
+                for (int e = 0; e <= T - 2; ++e) {
+#pragma unroll
+                  for (int r = 0; r < 4; ++r) {
+                    const int li = 4 * w + r;
+                    if (lane - li == e) Xs[li * T + lane] = e == 0 ? 0u : (key[r] & ~31u) + (wt[r] << 5);
+                  }
+                  bar_compute();
+#pragma unroll
+                  for (int r = 0; r < 4; ++r) {
+                    const int li = 4 * w + r;
+                    const int f = lane - li;
+                    // split k1 = li + e: left operand on diagonal e, right on f - e - 1
+                    const bool v1 = f > e && f - e - 1 <= e;
+                    const int k1 = v1 ? li + e : 0;
+                    const uint32_t c1 = Xs[li * T + k1] + pij[r] * finPKI[k1] + (uint32_t)k1;
+                    const uint32_t n1 = __viaddmin_u32(c1, Xs[(k1 + 1) * T + lane], key[r]);
+                    // split k2 = lane - 1 - e: right operand on diagonal e, left on f - 1 - e
+                    const bool v2 = f > e && f - 1 - e < e;
+                    const int k2 = v2 ? lane - 1 - e : 0;
+                    const uint32_t c2 = Xs[li * T + k2] + pij[r] * finPKI[k2] + (uint32_t)k2;
+                    const uint32_t n2 = __viaddmin_u32(c2, Xs[(k2 + 1) * T + lane], v1 ? n1 : key[r]);
+                    key[r] = v2 ? n2 : (v1 ? n1 : key[r]);
+                  }
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                  cb[r] = key[r] == 0xFFFFFFFFu ? ~0ull
+                                                : ((unsigned long long)(key[r] >> 5) << KB) | (unsigned)(IT + (key[r] & 31u));
+                keyed = true;
+              }
+            }
+#pragma unroll 1
+            for (int e = 0; e <= T - 2 && !keyed; ++e) {
 #pragma unroll
               for (int r = 0; r < 4; ++r) {
                 const int li = 4 * w + r;
