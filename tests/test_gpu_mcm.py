@@ -350,3 +350,17 @@ def test_int32_rate_probe(dp):
     native.check(lib.dp_measure_int32_rates(nine, 9, st))
     assert nine[9] == -1.0 and nine[5] > 0
     assert lib.dp_measure_int32_rates(nine, 8, st) == 1
+
+
+@pytest.mark.parametrize("n, hi", [(129, 101), (97, 111), (129, 102), (65, 160)])
+def test_diagonal_tile_keys_at_the_packing_limit(dp, n, hi):
+    """The diagonal tiles keep 32-bit (value << 5) + split keys when the
+    cost bound (n - 1) max(p)^3 is below 2^27 (packing shift 5), and 64-bit
+    keys otherwise. Chains just below the limit (127 * 101^3 and 96 * 111^3
+    below 2^27, keys near 2^32) and just above it (127 * 102^3, 64 * 160^3),
+    with dims at the maximum in every tile, against the oracle."""
+    bound = (n - 1) * hi ** 3
+    p = inputs.mcm_dims(n, hi - 3, hi, seed=7 * n + hi)
+    p[::5] = hi
+    assert (bound < (1 << 27)) == ((n, hi) in [(129, 101), (97, 111)])
+    _check(dp, p, "i32")
